@@ -1,0 +1,255 @@
+"""Pins of the oracle against what the paper and the mathematics fix.
+
+Each test names what fixes its expected value: the paper's printed W^2(L,0),
+closed forms of deterministic parameter corners, invariants of height
+functions (periodicity, zero curl, parity), library routines (numpy, scipy,
+Python's Fraction) or binomial statistics.
+"""
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _heights_y_first(X, Y, H0):
+    """Heights along the other path: down column 0 first, then along each row."""
+    sx = 2 * X.astype(np.int64) - 1
+    sy = 2 * Y.astype(np.int64) - 1
+    L = X.shape[0]
+    col0 = H0 + np.concatenate([[0], np.cumsum(sy[:-1, 0])])
+    h = np.zeros((L, L), np.int64)
+    h[:, 0] = col0
+    h[:, 1:] = col0[:, None] + np.cumsum(sx[:, :-1], axis=1)
+    return h
+
+
+def _check_invariants(sim):
+    X, Y, L = sim.X, sim.Y, sim.L
+    sx = 2 * X.astype(np.int64) - 1
+    sy = 2 * Y.astype(np.int64) - 1
+    # periodic heights: every row of sigma_x and every column of sigma_y sums to 0
+    assert np.all(sx.sum(axis=1) == 0)
+    assert np.all(sy.sum(axis=0) == 0)
+    # zero curl on every plaquette: sx(x,y) + sy(x+1,y) == sy(x,y) + sx(x,y+1)
+    assert np.array_equal(sx + np.roll(sy, -1, axis=1), sy + np.roll(sx, -1, axis=0))
+    # half of the bonds of each plane point up
+    assert int(X.sum()) == L * L // 2 and int(Y.sum()) == L * L // 2
+    h = sim.heights()
+    # the two summation paths of Eq. (3) agree
+    assert np.array_equal(h, _heights_y_first(X, Y, sim.H0))
+    # height parity is conserved: h == x + y (mod 2)
+    yy, xx = np.mgrid[0:L, 0:L]
+    assert np.all((h - xx - yy) % 2 == 0)
+    return h
+
+
+@pytest.mark.parametrize("p,q,s_sel,k_max,want", [
+    (1.0, 0.0, 0.5, 32, (1, 1, 0)),
+    (1.0, 0.0, 1.0, 32, (0, 1, 0)),
+    (0.0, 0.0, 0.5, 32, (0, 0, 0)),
+    (0.75, 0.25, 0.5, 32, (3, 3, 1)),
+    (0.5, 0.5, 0.5, 32, (2, 1, 1)),
+    (0.5, 0.5, 1.0, 32, (1, 1, 1)),
+])
+def test_thresholds_dyadic(orc, p, q, s_sel, k_max, want):
+    assert orc.thresholds(p, q, s_sel, k_max) == want
+
+
+@pytest.mark.parametrize("p,q,s_sel,k_max", [
+    (0.95, 0.05, 0.5, 32), (0.9, 0.1, 1.0, 32), (0.3, 0.7, 0.5, 12), (1 / 3, 0.0, 1.0, 7)])
+def test_thresholds_rounded(orc, p, q, s_sel, k_max):
+    """Non-dyadic probabilities: k = k_max, P = round-half-even(p_eff * 2^k), done
+    here with exact rationals (Fraction) and Python's round."""
+    k, P, Q = orc.thresholds(p, q, s_sel, k_max)
+    pe = Fraction(s_sel * p)  # the double product, exactly
+    qe = Fraction(s_sel * q)
+    assert k == k_max
+    assert P == round(pe * 2**k_max) and Q == round(qe * 2**k_max)
+
+
+def test_thresholds_reject_out_of_range(orc):
+    for args in [(1.5, 0, 0.5, 32), (-0.1, 0, 0.5, 32), (1, 0, 0.0, 32), (1, 0, 0.5, 33)]:
+        with pytest.raises(ValueError):
+            orc.thresholds(*args)
+
+
+def test_flat_start_width_is_one_quarter(orc):
+    """Sec. III: the striped start has W^2(L,0) = 1/4 (golden fixture)."""
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "flat_start.txt"))
+            if l.strip() and not l.startswith("#")]
+    for L, w2 in rows:
+        sim = orc.Sim(int(L), 1.0, 0.0, 1)
+        assert sim.width2() == float(w2)
+        h = sim.heights()
+        yy, xx = np.mgrid[0:int(L), 0:int(L)]
+        assert np.array_equal(h, (xx + yy) % 2)
+
+
+@pytest.mark.parametrize("L,p,q,s_sel,seed", [
+    (32, 1.0, 0.0, 0.5, 1), (30, 0.75, 0.25, 0.5, 2), (64, 0.95, 0.05, 0.5, 3),
+    (16, 0.5, 0.5, 1.0, 4), (48, 0.3, 0.6, 0.8, 5)])
+def test_invariants_and_local_changes(orc, L, p, q, s_sel, seed):
+    sim = orc.Sim(L, p, q, seed, s_sel=s_sel)
+    h = _check_invariants(sim)
+    yy, xx = np.mgrid[0:L, 0:L]
+    for _ in range(25):
+        for s in (0, 1):
+            before = h
+            hb = np.pad(before, 1, mode="wrap")
+            nbrs = np.stack([hb[1:-1, :-2], hb[1:-1, 2:], hb[:-2, 1:-1], hb[2:, 1:-1]])
+            is_min = np.all(nbrs == before + 1, axis=0)
+            is_max = np.all(nbrs == before - 1, axis=0)
+            sim.halfsweep(s)
+            h = _check_invariants(sim)
+            d = h - before
+            # only active sites change; minima by +2, maxima by -2
+            assert np.all(d[(xx + yy) % 2 != s] == 0)
+            assert np.all(np.isin(d, (-2, 0, 2)))
+            assert np.all(is_min[d == 2]) and np.all(is_max[d == -2])
+        sim.t += 1
+
+
+def test_closed_form_deterministic_growth(orc):
+    """s_sel = 1, p = 1, q = 0: every minimum rises each half-sweep, so the
+    surface moves up by 2 per sweep: S1 = N/2 + 2Nt and W^2 = 1/4 for all t."""
+    L = 32
+    N = L * L
+    sim = orc.Sim(L, 1.0, 0.0, 5, s_sel=1.0)
+    for t in range(1, 12):
+        sim.sweep(1)
+        S1, _ = sim.sums()
+        assert S1 == N // 2 + 2 * N * t
+        assert sim.width2() == 0.25
+
+
+def test_closed_form_deterministic_etching(orc):
+    """s_sel = 1, p = 0, q = 1: half-sweep 0 of sweep 1 finds only minima and
+    does nothing; from then on every maximum drops, so after t >= 1 sweeps even
+    sites sit at -2(t-1) and odd sites at 1 - 2t: S1 = 3N/2 - 2Nt, W^2 = 1/4."""
+    L = 16
+    N = L * L
+    sim = orc.Sim(L, 0.0, 1.0, 9, s_sel=1.0)
+    for t in range(1, 10):
+        sim.sweep(1)
+        S1, _ = sim.sums()
+        assert S1 == 3 * N // 2 - 2 * N * t
+        assert sim.width2() == 0.25
+
+
+def test_closed_form_frozen(orc):
+    """p = q = 0: nothing ever changes."""
+    sim = orc.Sim(32, 0.0, 0.0, 3)
+    X0, Y0 = sim.X.copy(), sim.Y.copy()
+    sim.sweep(5)
+    assert np.array_equal(sim.X, X0) and np.array_equal(sim.Y, Y0) and sim.H0 == 0
+
+
+def test_order_independence(orc):
+    """Sites of one sublattice share no bond: any visiting order gives the same state."""
+    rng = np.random.default_rng(0)
+    a = orc.Sim(24, 0.75, 0.25, 11)
+    a.sweep(7)
+    for s in (0, 1):
+        b = orc.Sim(24, 0.75, 0.25, 11)
+        b.X, b.Y, b.H0, b.t = a.X.copy(), a.Y.copy(), a.H0, a.t
+        active = np.array([y * 24 + x for y in range(24) for x in range(24)
+                           if (x + y) % 2 == s], np.int64)
+        order = rng.permutation(active)
+        import ctypes
+        H0 = ctypes.c_int64(b.H0)
+        assert orc.lib().orc_halfsweep_ordered(b.L, b.X, b.Y, ctypes.byref(H0), b.seed,
+                                               b.t, s, b.k, b.P, b.Q, order,
+                                               len(order)) == 0
+        a.halfsweep(s)
+        assert np.array_equal(a.X, b.X) and np.array_equal(a.Y, b.Y) and a.H0 == H0.value
+
+
+@pytest.mark.parametrize("p,q,s_sel", [(0.75, 0.25, 0.5), (0.95, 0.05, 0.5), (1.0, 0.0, 0.5)])
+def test_acceptance_rates(orc, p, q, s_sel):
+    """Fractions of active minima (maxima) that move match s_sel*p (s_sel*q)
+    within 5 binomial standard deviations."""
+    L = 128
+    sim = orc.Sim(L, p, q, 21, s_sel=s_sel)
+    sim.sweep(20)
+    nmin = nmin_acc = nmax = nmax_acc = 0
+    yy, xx = np.mgrid[0:L, 0:L]
+    for _ in range(30):
+        for s in (0, 1):
+            h = sim.heights()
+            hb = np.pad(h, 1, mode="wrap")
+            nbrs = np.stack([hb[1:-1, :-2], hb[1:-1, 2:], hb[:-2, 1:-1], hb[2:, 1:-1]])
+            act = (xx + yy) % 2 == s
+            is_min = np.all(nbrs == h + 1, axis=0) & act
+            is_max = np.all(nbrs == h - 1, axis=0) & act
+            sim.halfsweep(s)
+            d = sim.heights() - h
+            nmin += int(is_min.sum())
+            nmin_acc += int((d[is_min] == 2).sum())
+            nmax += int(is_max.sum())
+            nmax_acc += int((d[is_max] == -2).sum())
+        sim.t += 1
+    for n, a, pr in [(nmin, nmin_acc, s_sel * p), (nmax, nmax_acc, s_sel * q)]:
+        if pr in (0.0, 1.0):
+            assert a == (n if pr == 1.0 else 0)
+        else:
+            assert n > 1000
+            assert abs(a - n * pr) < 5 * np.sqrt(n * pr * (1 - pr))
+
+
+def test_width_and_moments_match_numpy_scipy(orc):
+    from scipy import stats
+    sim = orc.Sim(64, 0.75, 0.25, 4)
+    sim.sweep(40)
+    h = sim.heights().astype(np.float64)
+    assert sim.width2() == pytest.approx(np.var(h), rel=1e-12)
+    sk, ku = sim.skew_kurt()
+    assert sk == pytest.approx(stats.skew(h, axis=None), rel=1e-9, abs=1e-12)
+    assert ku == pytest.approx(stats.kurtosis(h, axis=None), rel=1e-9, abs=1e-12)
+    S = sim.power_sums()
+    d = sim.heights() - sim.H0
+    assert S == [int((d.astype(object) ** n).sum()) for n in range(1, 5)]
+
+
+def test_sums_are_exact_beyond_int64(orc):
+    """A surface raised by ~2^30 keeps exact 128-bit sums (S2 ~ 2^72)."""
+    sim = orc.Sim(64, 1.0, 0.0, 1)
+    sim.sweep(3)
+    h = sim.heights()
+    sim.H0 += 2 ** 31  # shift the whole surface (heights are anchored at H0)
+    S1, S2 = sim.sums()
+    hh = (h + 2 ** 31).astype(object)
+    assert S1 == int(hh.sum()) and S2 == int((hh * hh).sum())
+    assert sim.width2() == pytest.approx(np.var(h.astype(np.float64)), rel=1e-12)
+
+
+def test_sample_times(orc):
+    for T, n in [(1000, 20), (10000, 40), (8192, 40), (50, 40)]:
+        ts = orc.sample_times(T, n)
+        assert ts[0] == 0 and ts[-1] == T and len(ts) == n + 1
+        assert all(b > a for a, b in zip(ts, ts[1:]))
+        # away from the forced +1 steps the times follow T^(j/(n-1))
+        for j in range(n):
+            v = round(T ** (j / (n - 1)))
+            assert ts[j + 1] >= v
+            if v > n:
+                assert ts[j + 1] == v
+    with pytest.raises(ValueError):
+        orc.sample_times(10, 40)
+
+
+def test_random_sequential_variant(orc):
+    """The random-sequential dynamics keeps the height-function invariants, and
+    with p = 1, q = 0 every accepted move raises a minimum by 2."""
+    sim = orc.Sim(32, 1.0, 0.0, 8)
+    for _ in range(10):
+        S1_before, _ = sim.sums()
+        sim.rs_sweep(1)
+        _check_invariants(sim)
+        S1, _ = sim.sums()
+        assert S1 > S1_before and (S1 - S1_before) % 2 == 0
+    sim = orc.Sim(32, 0.5, 0.5, 8)
+    sim.rs_sweep(20)
+    _check_invariants(sim)
