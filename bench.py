@@ -1,0 +1,317 @@
+"""Benchmark of the octahedron-model hot path on GB300.
+
+Workload (the L = 2^17 growth run): L = 131072 periodic lattice (2^34 sites,
+4 GiB of bond planes), striped start, p = 1, q = 0, selection 1/2, Philox seed
+11. One step = 256 sweeps (one fused sweep-kernel launch each) followed by one
+measurement: height reconstruction and the exact sums sum h, sum h^2 that give
+W^2. 32 steps = the full 2^13-sweep run; the timed steps start from t = 0.
+
+Metric: site-update attempts per second (every active-sublattice visit counts
+as one attempt), reported in GUPS = 1e9 attempts/s.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0). Under torchrun (N > 1) every rank runs its own
+independent lattice (replicas, no data-path collective; weak scaling).
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L_DEFAULT = 1 << 17
+SEED = 11
+SWEEPS_PER_STEP = 256
+METRIC = "site-update attempts/s (GUPS)"
+UNIT = "GUPS (1e9 site-update attempts/s)"
+BYTES_PER_SITE_SWEEP = 0.5  # read 2 bits + write 2 bits per site, one pass
+
+# dram__bytes_read.sum + dram__bytes_write.sum of one sweep-kernel launch, taken
+# by ncu on an L = 32768 lattice and scaled by the site count to L = 2^17, for
+# the kernel source with this SHA-256 (None: not measured for this source).
+TRAFFIC_BYTES_PER_SITE = None
+TRAFFIC_SOURCE_SHA = None
+
+
+def _kernel_sha():
+    p = os.path.join(ROOT, "paper_1110_6745_gb300", "csrc", "sweep_stream.cu")
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = str(gpu_index)
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu, "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist_init(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl != "reference" else "gloo"
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def _barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(world, v, device=None):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_baseline(L=16384, sweeps=10):
+    """The CPU oracle as it stands on a bounded sample of the workload."""
+    import oracle
+    sim = oracle.Sim(L, 1.0, 0.0, SEED)
+    t0 = time.perf_counter()
+    sim.sweep(sweeps)
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": L * L * sweeps / dt / 1e9, "unit": UNIT, "cores": cores,
+            "kind": "oracle",
+            "sample": "L=%d striped start, p=1, q=0, s_sel=1/2, seed=%d, %d sweeps "
+                      "(%.3g attempts, %.1f s), OpenMP over rows" % (L, SEED, sweeps,
+                                                                     L * L * sweeps, dt)}
+
+
+def run_reference(args, world, rank):
+    """--impl reference: the CPU oracle timed on the host cores (rank 0 only)."""
+    if rank != 0:
+        return
+    import oracle
+    L, per_step = 8192, 2
+    sim = oracle.Sim(L, 1.0, 0.0, SEED)
+    sim.sweep(per_step * args.warmup)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sim.sweep(per_step)
+        sim.width2()
+    dt = time.perf_counter() - t0
+    attempts = L * L * per_step * args.steps
+    value = attempts / dt / 1e9
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic", "impl": "reference",
+        "config": {"workload": "octahedron growth, striped start, p=1 q=0 s_sel=1/2 "
+                               "(bounded CPU sample: L=8192, 2 sweeps + W^2 per step)",
+                   "L": L, "sweeps_per_step": per_step},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "L=8192, %d sweeps + one W^2 per step, %d steps"
+                                   % (per_step, args.steps)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args, world, rank, local):
+    import torch
+
+    import paper_1110_6745_gb300 as okz
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    L = args.L
+    N = L * L
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        sim = okz.Simulation(L, 1.0, 0.0, seed=SEED + rank, torch_buffer=True)
+    assert sim.info().kernel == okz.OKZ_KERNEL_STREAM
+    # checkpoint of the striped start, kept on the device
+    start_planes = torch.empty(2 * L * L // 32, dtype=torch.int32, device=dev)
+    sim.state(out=start_planes)
+
+    def step(ev_a=None, ev_b=None):
+        if ev_a is not None:
+            ev_a.record(stream)
+        sim.sweep(SWEEPS_PER_STEP)
+        if ev_b is not None:
+            ev_b.record(stream)
+        return sim.width2()
+
+    for _ in range(args.warmup):
+        step()
+    sim.restore(start_planes, 0, 0)
+    torch.cuda.synchronize(dev)
+
+    sweep_evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                 for _ in range(args.steps)]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    _barrier(world)
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    t_start.record(stream)
+    records = []
+    for k in range(args.steps):
+        records.append(step(*sweep_evs[k]))
+    t_end.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    _barrier(world)
+    elapsed_ms = t_start.elapsed_time(t_end)
+    sweep_ms = sum(a.elapsed_time(b) for a, b in sweep_evs)
+    elapsed_ms = _max_over_ranks(world, elapsed_ms, dev)
+    sweeps = SWEEPS_PER_STEP * args.steps
+    value = world * N * sweeps / (elapsed_ms / 1e3) / 1e9
+    launches = args.steps * (SWEEPS_PER_STEP + 3)  # sweeps + 3 measurement kernels
+
+    # roofline of the sweep kernel: algorithmic bytes per launch / launch time
+    per_launch_s = sweep_ms / 1e3 / sweeps
+    alg_bytes = BYTES_PER_SITE_SWEEP * N
+    achieved = alg_bytes / per_launch_s / 1e9
+    peak, peak_kind = _peaks()
+    traffic = None
+    if TRAFFIC_BYTES_PER_SITE is not None and TRAFFIC_SOURCE_SHA == _kernel_sha():
+        traffic = TRAFFIC_BYTES_PER_SITE * N
+
+    # end to end through the C-ABI with host buffers: each step restores the
+    # lattice from pinned host memory, sweeps, and reads back the exact sums
+    e2e_steps = min(args.steps, 8)
+    host_planes = torch.empty(2 * L * L // 32, dtype=torch.int32, pin_memory=True)
+    host_planes.copy_(start_planes.cpu())
+    torch.cuda.synchronize(dev)
+    _barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        sim.restore(host_planes, 0, 0)
+        sim.sweep(SWEEPS_PER_STEP)
+        sim.width2()
+    torch.cuda.synchronize(dev)
+    e2e_s = _max_over_ranks(world, time.perf_counter() - t0, dev)
+    e2e_value = world * N * SWEEPS_PER_STEP * e2e_steps / e2e_s / 1e9
+    h2d = L * L // 4 + 8            # both planes + H0
+    d2h = 256 + 4                   # control block (sums, H0) + error word
+
+    w2_final = records[-1][2]
+    sim.close()
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": "octahedron growth run L=2^17 (2^34 sites), striped start, "
+                               "p=1 q=0 s_sel=1/2, seed=11; step = 256 sweeps + exact W^2",
+                   "L": L, "sweeps_per_step": SWEEPS_PER_STEP, "t_range": [0, sweeps],
+                   "l2": "inputs larger than L2 (2 x 4 GiB ping-pong planes)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "sweep_stream_kernel", "peak_kind": peak_kind,
+                     "bytes_per_launch": alg_bytes,
+                     "launch_ms": per_launch_s * 1e3},
+        "sweep_gups": N / per_launch_s / 1e9,
+        "gpu_launches": launches,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "steps": e2e_steps},
+        "w2_final": w2_final,
+        "clocks": clk,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=32)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="okz", choices=["okz", "reference"])
+    ap.add_argument("--L", type=int, default=L_DEFAULT)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = _dist_init(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_gpu(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,198 @@
+/*
+ * okz.h -- C-ABI of the GB300 octahedron-model library.
+ *
+ * The library simulates the 2+1-dimensional octahedron model of
+ * J. Kelling and G. Odor, "Extremely large scale simulation of a
+ * Kardar-Parisi-Zhang model using graphics cards" (arXiv:1110.6745):
+ * integer heights h(x,y) on an L x L periodic lattice whose neighbours differ
+ * by exactly 1, held as two slope bit-planes (Sec. II: two bits per site).
+ * A local minimum is raised by 2 with probability p, a local maximum lowered
+ * by 2 with probability q (Sec. I, Eq. (2)).
+ *
+ * Conventions shared by every entry point:
+ *  - Every call returns an okz_status. Output arguments are written only when
+ *    the call returns OKZ_OK. okz_last_error() gives a thread-local message
+ *    for the most recent failure of the calling thread.
+ *  - A simulation is owned by the library (opaque handle). Caller buffers
+ *    passed in are only read or written during the call, unless stated.
+ *  - Work is ordered on the simulation's CUDA stream. Calls marked
+ *    "synchronizing" wait for that stream before returning.
+ *  - Pointers are plain host or device addresses as stated per argument;
+ *    "device" means memory of the CUDA device current when the simulation was
+ *    created.
+ *
+ * Bit-plane layout (the only state format that crosses this boundary):
+ *   plane X holds sigma_x(x,y) = h(x+1,y) - h(x,y), plane Y holds
+ *   sigma_y(x,y) = h(x,y+1) - h(x,y); a set bit means +1, a clear bit -1.
+ *   Each plane is L rows of L/32 little-endian uint32 words, row-major; bit b
+ *   of word w of row y is the bond at x = 32*w + b. A state buffer is the X
+ *   plane followed by the Y plane: 2 * L * L / 8 bytes.
+ *
+ * Dynamics (one sweep = one Monte Carlo step, Sec. II):
+ *   sweep t runs half-sweep s = 0 (every site with (x+y) even) and then
+ *   half-sweep s = 1. A site touches only its four bonds, and sites of one
+ *   sublattice share no bond, so a half-sweep is order independent.
+ *   Every active site is selected with probability s_sel; a selected minimum
+ *   (maximum) moves when U < P (U < Q). U is a k-bit uniform, and k, P, Q
+ *   come from p_eff = s_sel * p, q_eff = s_sel * q: k is the smallest k <=
+ *   k_max with p_eff 2^k and q_eff 2^k integral, else k = k_max with
+ *   round-half-even thresholds.
+ *   Random draws: for site index i = y*L + x, group g = i / 128, word
+ *   j = (i mod 128) / 32, bit b = i mod 32, level m of the draw at sweep t is
+ *   bit b of word j of Philox4x32-10 (Salmon et al., SC'11) with counter
+ *   (g mod 2^32, g / 2^32, t, m) and key (seed mod 2^32, seed / 2^32);
+ *   U = sum_m bit_m 2^(k-1-m), most significant level first.
+ */
+#ifndef OKZ_H
+#define OKZ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum okz_status {
+    OKZ_OK = 0,
+    OKZ_EINVAL = 1,       /* bad argument (odd L, p > 1, null pointer, ...)        */
+    OKZ_ENOMEM = 2,       /* device or host allocation failed / buffer too small    */
+    OKZ_ECUDA = 3,        /* a CUDA call failed; see okz_last_error()               */
+    OKZ_ETIMEOUT = 4,     /* a bounded device-side wait gave up                     */
+    OKZ_EBUSY = 5,        /* no free slot or memory for admission                   */
+    OKZ_EOVERFLOW = 6,    /* sweep counter would pass 2^32 - 1                      */
+    OKZ_EUNSUPPORTED = 7  /* valid request this build does not handle (e.g. L % 32) */
+} okz_status;
+
+/* Two's-complement 128-bit integer: value = hi * 2^64 + lo. */
+typedef struct okz_i128 {
+    uint64_t lo;
+    int64_t hi;
+} okz_i128;
+
+/* Which sweep kernel a simulation uses. AUTO picks STREAM when L is a
+ * multiple of 4096 and at most 131072, else PLAIN. Both give bit-identical
+ * results. */
+enum {
+    OKZ_KERNEL_AUTO = 0,
+    OKZ_KERNEL_PLAIN = 1,  /* one in-place launch per half-sweep                 */
+    OKZ_KERNEL_STREAM = 2  /* one launch per sweep, TMA-staged rows, ping-pong    */
+};
+
+typedef struct okz_params {
+    int64_t L;      /* linear size; the GPU needs L % 32 == 0 and L >= 32         */
+    double p;       /* attachment probability, minimum -> maximum, in [0, 1]      */
+    double q;       /* detachment probability, maximum -> minimum, in [0, 1]      */
+    uint64_t seed;  /* Philox key                                                  */
+    double s_sel;   /* selection probability of an active site, (0, 1]; 0.5      */
+    int32_t k_max;  /* largest acceptance precision in bits, 1..32; 32            */
+    int32_t kernel; /* OKZ_KERNEL_*                                                */
+} okz_params;
+
+typedef struct okz_info {
+    int64_t L;
+    uint64_t t;           /* completed sweeps                                  */
+    int64_t H0;           /* h(0,0)                                            */
+    int32_t k;            /* acceptance precision in bits                      */
+    int32_t kernel;       /* OKZ_KERNEL_PLAIN or OKZ_KERNEL_STREAM             */
+    uint64_t P, Q;        /* thresholds: accept iff U < P (min) / U < Q (max)  */
+    size_t device_bytes;  /* device memory held by the simulation              */
+} okz_info;
+
+typedef struct okz_sim okz_sim;
+
+/* Fills *prm with the defaults: L = 0, p = 1, q = 0, seed = 0, s_sel = 0.5,
+ * k_max = 32, kernel = AUTO. */
+void okz_params_init(okz_params *prm);
+
+/* Device bytes a simulation of size L needs when memory is passed to
+ * okz_create_ex: two state buffers (ping-pong, L*L/4 bytes each), L int64 of
+ * column heights and a 256-byte control block, each 256-byte aligned.
+ * Returns 0 for an invalid L. */
+size_t okz_device_bytes(int64_t L);
+
+/* Creates a simulation on the current CUDA device with the striped start
+ * h(x,y) = (x+y) mod 2, H0 = 0, t = 0 (Sec. III: "half filled (striped)",
+ * W^2 = 1/4), s_sel = 0.5 and k_max = 32. The library allocates the device
+ * memory and a non-blocking stream. L even, L % 32 == 0, L >= 32; p, q in
+ * [0, 1]. Errors: EINVAL, EUNSUPPORTED, ENOMEM, ECUDA. */
+okz_status okz_create(int64_t L, double p, double q, uint64_t seed, okz_sim **out);
+
+/* As okz_create with every parameter given. If dev_buf is not NULL it must
+ * be a device buffer of at least okz_device_bytes(L) bytes, 256-byte
+ * aligned, which the caller keeps alive until okz_destroy; otherwise the
+ * library allocates. stream is a cudaStream_t (NULL = the library creates
+ * its own non-blocking stream); all work of this simulation is ordered on
+ * it. Errors: EINVAL, EUNSUPPORTED, ENOMEM, ECUDA. */
+okz_status okz_create_ex(const okz_params *prm, void *dev_buf, size_t bytes,
+                         void *stream, okz_sim **out);
+
+/* Enqueues n >= 0 sweeps (Sec. II: one sweep = one MCS) on the simulation's
+ * stream and returns without waiting. Errors: EINVAL (n < 0), EOVERFLOW
+ * (t + n > 2^32 - 1; nothing is enqueued), ECUDA (launch failure). */
+okz_status okz_sweep(okz_sim *sim, int64_t n);
+
+/* Synchronizing. Reconstructs the heights from the slopes (Sec. I, Eq. (3),
+ * anchored at H0 = h(0,0)) and returns the exact sums S1 = sum h,
+ * S2 = sum h^2 and the squared width of Sec. I, Eq. (4),
+ *   W2 = (N*S2 - S1^2) / N^2,  N = L*L,
+ * with the numerator formed exactly in 128-bit integers and rounded once to
+ * double. Any output pointer may be NULL. Errors: ECUDA, ETIMEOUT. */
+okz_status okz_width2(okz_sim *sim, okz_i128 *S1, okz_i128 *S2, double *W2);
+
+/* Synchronizing. Exact central power sums S_n = sum (h - H0)^n, n = 1..4
+ * (Sk[0..3]), and from them W2, the skewness m3/m2^1.5 and the excess
+ * kurtosis m4/m2^2 - 3 of the height distribution, with mu = S1/N,
+ * m2 = S2/N - mu^2, m3 = S3/N - 3 mu S2/N + 2 mu^3,
+ * m4 = S4/N - 4 mu S3/N + 6 mu^2 S2/N - 3 mu^4 in long double.
+ * Needs L <= 131072. Any output pointer may be NULL. */
+okz_status okz_moments(okz_sim *sim, okz_i128 Sk[4], double *W2, double *skew,
+                       double *kurt);
+
+/* Synchronizing. Writes h(x, y) for rows y0 .. y0+ny-1 (Sec. I, Eq. (3)) as
+ * int32, row-major, ny * L values, to out (device memory if out_is_device,
+ * else host memory). 0 <= y0, y0 + ny <= L. Errors: EINVAL, EOVERFLOW (some
+ * |h| >= 2^31; out is then undefined), ECUDA. */
+okz_status okz_heights(okz_sim *sim, int64_t y0, int64_t ny, int32_t *out,
+                       int out_is_device);
+
+/* Synchronizing. Copies the state buffer (X plane then Y plane, layout
+ * above) to planes_out (device memory if out_is_device, else host) and
+ * returns H0 and t (either pointer may be NULL). */
+okz_status okz_state(okz_sim *sim, uint32_t *planes_out, int out_is_device,
+                     int64_t *H0, uint64_t *t);
+
+/* Replaces the state with planes (same layout; device memory if
+ * in_is_device, else host), H0 and t. The planes must describe a height
+ * function (zero row sums of sigma_x, zero column sums of sigma_y, zero
+ * curl); this is not checked. Synchronizing. */
+okz_status okz_restore(okz_sim *sim, const uint32_t *planes, int in_is_device,
+                       int64_t H0, uint64_t t);
+
+/* Fills *info. Synchronizing (H0 lives on the device). */
+okz_status okz_get_info(okz_sim *sim, okz_info *info);
+
+/* Waits for the simulation's stream and reports device-side errors
+ * (ETIMEOUT when a bounded wait inside a kernel gave up). */
+okz_status okz_synchronize(okz_sim *sim);
+
+/* The simulation's stream (a cudaStream_t). */
+void *okz_stream(okz_sim *sim);
+
+/* Waits for outstanding work, frees what the library allocated, and
+ * destroys the handle. NULL is accepted. */
+okz_status okz_destroy(okz_sim *sim);
+
+/* Message of the calling thread's most recent failure ("" if none). */
+const char *okz_last_error(void);
+
+/* Acceptance precision and thresholds for (p, q, s_sel, k_max), the rule
+ * stated above; the host computation every simulation uses. */
+okz_status okz_thresholds(double p, double q, double s_sel, int32_t k_max,
+                          int32_t *k, uint64_t *P, uint64_t *Q);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OKZ_H */

@@ -1,0 +1,287 @@
+"""Python binding of the okz C-ABI (include/okz.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls; all work runs
+in the CUDA library ``_build/libokz.so`` (build it with
+``python -c "import __graft_entry__ as g; g.build()"``). There is no CPU
+fallback: when the library is missing, loading fails loudly.
+
+PyTorch is optional plumbing: ``create_on_torch`` places a simulation in a
+torch-allocated device buffer on torch's current stream.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libokz.so")
+
+OKZ_OK, OKZ_EINVAL, OKZ_ENOMEM, OKZ_ECUDA, OKZ_ETIMEOUT, OKZ_EBUSY, OKZ_EOVERFLOW, \
+    OKZ_EUNSUPPORTED = range(8)
+OKZ_KERNEL_AUTO, OKZ_KERNEL_PLAIN, OKZ_KERNEL_STREAM = 0, 1, 2
+STATUS_NAMES = {0: "OKZ_OK", 1: "OKZ_EINVAL", 2: "OKZ_ENOMEM", 3: "OKZ_ECUDA",
+                4: "OKZ_ETIMEOUT", 5: "OKZ_EBUSY", 6: "OKZ_EOVERFLOW", 7: "OKZ_EUNSUPPORTED"}
+
+
+class OkzError(RuntimeError):
+    def __init__(self, status, func, msg):
+        self.status = status
+        super().__init__("%s failed: %s: %s" % (func, STATUS_NAMES.get(status, status), msg))
+
+
+class okz_i128(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_uint64), ("hi", ctypes.c_int64)]
+
+    def value(self):
+        return (int(self.hi) << 64) | int(self.lo)
+
+
+class okz_params(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int64), ("p", ctypes.c_double), ("q", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("s_sel", ctypes.c_double),
+                ("k_max", ctypes.c_int32), ("kernel", ctypes.c_int32)]
+
+
+class okz_info(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int64), ("t", ctypes.c_uint64), ("H0", ctypes.c_int64),
+                ("k", ctypes.c_int32), ("kernel", ctypes.c_int32), ("P", ctypes.c_uint64),
+                ("Q", ctypes.c_uint64), ("device_bytes", ctypes.c_size_t)]
+
+
+# C signatures: name -> (restype, argtypes)
+_c = ctypes
+_vp = _c.c_void_p
+_SIGS = {
+    "okz_params_init": (None, [_c.POINTER(okz_params)]),
+    "okz_device_bytes": (_c.c_size_t, [_c.c_int64]),
+    "okz_create": (_c.c_int, [_c.c_int64, _c.c_double, _c.c_double, _c.c_uint64,
+                              _c.POINTER(_vp)]),
+    "okz_create_ex": (_c.c_int, [_c.POINTER(okz_params), _vp, _c.c_size_t, _vp,
+                                 _c.POINTER(_vp)]),
+    "okz_sweep": (_c.c_int, [_vp, _c.c_int64]),
+    "okz_width2": (_c.c_int, [_vp, _c.POINTER(okz_i128), _c.POINTER(okz_i128),
+                              _c.POINTER(_c.c_double)]),
+    "okz_moments": (_c.c_int, [_vp, _c.POINTER(okz_i128), _c.POINTER(_c.c_double),
+                               _c.POINTER(_c.c_double), _c.POINTER(_c.c_double)]),
+    "okz_heights": (_c.c_int, [_vp, _c.c_int64, _c.c_int64, _vp, _c.c_int]),
+    "okz_state": (_c.c_int, [_vp, _vp, _c.c_int, _c.POINTER(_c.c_int64),
+                             _c.POINTER(_c.c_uint64)]),
+    "okz_restore": (_c.c_int, [_vp, _vp, _c.c_int, _c.c_int64, _c.c_uint64]),
+    "okz_get_info": (_c.c_int, [_vp, _c.POINTER(okz_info)]),
+    "okz_synchronize": (_c.c_int, [_vp]),
+    "okz_stream": (_vp, [_vp]),
+    "okz_destroy": (_c.c_int, [_vp]),
+    "okz_last_error": (_c.c_char_p, []),
+    "okz_thresholds": (_c.c_int, [_c.c_double, _c.c_double, _c.c_double, _c.c_int32,
+                                  _c.POINTER(_c.c_int32), _c.POINTER(_c.c_uint64),
+                                  _c.POINTER(_c.c_uint64)]),
+}
+
+_lib = None
+
+
+def lib():
+    """The loaded libokz.so. Raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libokz.so is missing (%s); build it with "
+                               "__graft_entry__.build()" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status, func):
+    if status != OKZ_OK:
+        raise OkzError(status, func, okz_last_error())
+
+
+def okz_last_error():
+    return lib().okz_last_error().decode()
+
+
+def okz_params_init(L=0, p=1.0, q=0.0, seed=0, s_sel=0.5, k_max=32, kernel=OKZ_KERNEL_AUTO):
+    prm = okz_params()
+    lib().okz_params_init(ctypes.byref(prm))
+    prm.L, prm.p, prm.q, prm.seed = int(L), float(p), float(q), int(seed)
+    prm.s_sel, prm.k_max, prm.kernel = float(s_sel), int(k_max), int(kernel)
+    return prm
+
+
+def okz_device_bytes(L):
+    return int(lib().okz_device_bytes(int(L)))
+
+
+def okz_thresholds(p, q, s_sel=0.5, k_max=32):
+    k, P, Q = ctypes.c_int32(), ctypes.c_uint64(), ctypes.c_uint64()
+    _check(lib().okz_thresholds(p, q, s_sel, k_max, ctypes.byref(k), ctypes.byref(P),
+                                ctypes.byref(Q)), "okz_thresholds")
+    return k.value, P.value, Q.value
+
+
+def okz_create(L, p, q, seed):
+    h = ctypes.c_void_p()
+    _check(lib().okz_create(int(L), float(p), float(q), int(seed), ctypes.byref(h)),
+           "okz_create")
+    return h
+
+
+def okz_create_ex(prm, dev_buf=None, nbytes=0, stream=None):
+    h = ctypes.c_void_p()
+    _check(lib().okz_create_ex(ctypes.byref(prm), dev_buf, int(nbytes), stream,
+                               ctypes.byref(h)), "okz_create_ex")
+    return h
+
+
+def okz_sweep(h, n):
+    _check(lib().okz_sweep(h, int(n)), "okz_sweep")
+
+
+def okz_width2(h):
+    """-> (S1, S2, W2) with S1 = sum h and S2 = sum h^2 as Python ints."""
+    S1, S2, W2 = okz_i128(), okz_i128(), ctypes.c_double()
+    _check(lib().okz_width2(h, ctypes.byref(S1), ctypes.byref(S2), ctypes.byref(W2)),
+           "okz_width2")
+    return S1.value(), S2.value(), W2.value
+
+
+def okz_moments(h):
+    """-> ([S1..S4] about H0, W2, skew, excess kurtosis)."""
+    Sk = (okz_i128 * 4)()
+    W2, sk, ku = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(lib().okz_moments(h, Sk, ctypes.byref(W2), ctypes.byref(sk), ctypes.byref(ku)),
+           "okz_moments")
+    return [s.value() for s in Sk], W2.value, sk.value, ku.value
+
+
+def okz_heights(h, y0, ny, L, out=None):
+    """Heights of rows y0..y0+ny-1. out: None (returns a numpy int32 array), a
+    numpy int32 array, or a CUDA torch int32 tensor (filled on the device)."""
+    if out is None:
+        out = np.empty((int(ny), int(L)), np.int32)
+    is_dev = 0
+    if isinstance(out, np.ndarray):
+        assert out.dtype == np.int32 and out.flags.c_contiguous and out.size >= ny * L
+        ptr = out.ctypes.data
+    else:  # torch tensor on the device
+        assert out.is_cuda and out.is_contiguous() and out.numel() >= ny * L
+        ptr, is_dev = out.data_ptr(), 1
+    _check(lib().okz_heights(h, int(y0), int(ny), ptr, is_dev), "okz_heights")
+    return out
+
+
+def okz_state(h, L, out=None):
+    """-> (planes, H0, t); planes is (2, L, L//32) uint32 (X plane, Y plane) or the
+    given output (numpy array or CUDA torch tensor of 2*L*L/32 uint32/int32)."""
+    if out is None:
+        out = np.empty((2, int(L), int(L) // 32), np.uint32)
+    is_dev = 0
+    if isinstance(out, np.ndarray):
+        assert out.nbytes >= 2 * L * L // 8 and out.flags.c_contiguous
+        ptr = out.ctypes.data
+    else:
+        assert out.is_cuda and out.is_contiguous()
+        ptr, is_dev = out.data_ptr(), 1
+    H0, t = ctypes.c_int64(), ctypes.c_uint64()
+    _check(lib().okz_state(h, ptr, is_dev, ctypes.byref(H0), ctypes.byref(t)), "okz_state")
+    return out, H0.value, t.value
+
+
+def okz_restore(h, planes, H0, t):
+    if isinstance(planes, np.ndarray):
+        planes = np.ascontiguousarray(planes, dtype=np.uint32)
+        ptr, is_dev = planes.ctypes.data, 0
+    else:
+        assert planes.is_contiguous()
+        ptr, is_dev = planes.data_ptr(), int(planes.is_cuda)
+    _check(lib().okz_restore(h, ptr, is_dev, int(H0), int(t)), "okz_restore")
+
+
+def okz_get_info(h):
+    info = okz_info()
+    _check(lib().okz_get_info(h, ctypes.byref(info)), "okz_get_info")
+    return info
+
+
+def okz_synchronize(h):
+    _check(lib().okz_synchronize(h), "okz_synchronize")
+
+
+def okz_stream(h):
+    return lib().okz_stream(h)
+
+
+def okz_destroy(h):
+    _check(lib().okz_destroy(h), "okz_destroy")
+
+
+class Simulation:
+    """Owning wrapper: a simulation handle plus the torch buffer it may live in."""
+
+    def __init__(self, L, p=1.0, q=0.0, seed=0, s_sel=0.5, k_max=32,
+                 kernel=OKZ_KERNEL_AUTO, torch_buffer=False, stream=None):
+        self.L = int(L)
+        self._buf = None
+        prm = okz_params_init(L, p, q, seed, s_sel, k_max, kernel)
+        if torch_buffer:
+            import torch
+            nbytes = okz_device_bytes(L)
+            self._buf = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+            base = self._buf.data_ptr()
+            aligned = (base + 255) & ~255
+            if stream is None:
+                stream = torch.cuda.current_stream().cuda_stream
+            self.h = okz_create_ex(prm, aligned, nbytes, stream)
+        else:
+            self.h = okz_create_ex(prm, None, 0, stream)
+
+    def sweep(self, n=1):
+        okz_sweep(self.h, n)
+
+    def width2(self):
+        return okz_width2(self.h)
+
+    def moments(self):
+        return okz_moments(self.h)
+
+    def heights(self, y0=0, ny=None, out=None):
+        return okz_heights(self.h, y0, self.L - y0 if ny is None else ny, self.L, out)
+
+    def state(self, out=None):
+        return okz_state(self.h, self.L, out)
+
+    def restore(self, planes, H0, t):
+        okz_restore(self.h, planes, H0, t)
+
+    def info(self):
+        return okz_get_info(self.h)
+
+    def synchronize(self):
+        okz_synchronize(self.h)
+
+    @property
+    def stream(self):
+        return okz_stream(self.h)
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            okz_destroy(self.h)
+            self.h = None
+            self._buf = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

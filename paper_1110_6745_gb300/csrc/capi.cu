@@ -1,0 +1,477 @@
+// capi.cu -- the C-ABI of include/okz.h: simulation handles, argument checks,
+// stream-ordered launches and the exact host-side finalization of W^2.
+#include <cuda_runtime.h>
+
+#include <cfenv>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "okz_internal.h"
+
+struct okz_sim {
+  okz_params prm;
+  okz::Accept acc;
+  int kernel;
+  int device;
+  cudaStream_t stream;
+  bool own_stream;
+  char *base;
+  bool own_mem;
+  okz::Layout lay;
+  uint32_t *planes[2];
+  int cur;
+  int64_t *hcol;
+  unsigned long long *partials;
+  okz::Ctrl *ctrl;
+  uint64_t t;
+};
+
+namespace okz {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+okz_status cuda_fail(cudaError_t e, const char *what) {
+  set_error(std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) +
+            ")");
+  return OKZ_ECUDA;
+}
+
+static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+Layout layout_for(int64_t L) {
+  Layout lay{};
+  lay.planes_bytes = (size_t)L * (size_t)L / 4;  // 2 bits per site
+  size_t off = 0;
+  lay.off_planes0 = off;
+  off = align256(off + lay.planes_bytes);
+  lay.off_planes1 = off;
+  off = align256(off + lay.planes_bytes);
+  lay.off_hcol = off;
+  off = align256(off + (size_t)L * sizeof(int64_t));
+  lay.off_partials = off;
+  off = align256(off + (size_t)kMaxReduceBlocks * 8 * sizeof(unsigned long long));
+  lay.off_ctrl = off;
+  off = align256(off + sizeof(Ctrl));
+  lay.total = off;
+  return lay;
+}
+
+static okz_status check_L(int64_t L) {
+  if (L < 2 || (L & 1)) {
+    set_error("L must be even and >= 2");
+    return OKZ_EINVAL;
+  }
+  if (L % 32 != 0 || L > (int64_t)1 << 20) {
+    set_error("this build needs L % 32 == 0 and L <= 2^20");
+    return OKZ_EUNSUPPORTED;
+  }
+  return OKZ_OK;
+}
+
+}  // namespace okz
+
+using namespace okz;
+
+static okz_i128 from_i128(__int128 v) {
+  okz_i128 r;
+  r.lo = (uint64_t)(unsigned __int128)v;
+  r.hi = (int64_t)(uint64_t)((unsigned __int128)v >> 64);
+  return r;
+}
+
+extern "C" {
+
+const char *okz_last_error(void) { return g_last_error.c_str(); }
+
+void okz_params_init(okz_params *prm) {
+  if (!prm) return;
+  prm->L = 0;
+  prm->p = 1.0;
+  prm->q = 0.0;
+  prm->seed = 0;
+  prm->s_sel = 0.5;
+  prm->k_max = 32;
+  prm->kernel = OKZ_KERNEL_AUTO;
+}
+
+okz_status okz_thresholds(double p, double q, double s_sel, int32_t k_max, int32_t *k,
+                          uint64_t *P, uint64_t *Q) {
+  if (!(p >= 0.0 && p <= 1.0 && q >= 0.0 && q <= 1.0)) {
+    set_error("p and q must lie in [0, 1]");
+    return OKZ_EINVAL;
+  }
+  if (!(s_sel > 0.0 && s_sel <= 1.0) || k_max < 1 || k_max > 32) {
+    set_error("s_sel must lie in (0, 1] and k_max in 1..32");
+    return OKZ_EINVAL;
+  }
+  const double pe = s_sel * p, qe = s_sel * q;
+  int kk = -1;
+  double a = 0, b = 0;
+  for (int j = 0; j <= k_max; ++j) {  // smallest exact precision
+    a = std::ldexp(pe, j);
+    b = std::ldexp(qe, j);
+    if (a == std::floor(a) && b == std::floor(b)) {
+      kk = j;
+      break;
+    }
+  }
+  if (kk < 0) {  // round half to even at k_max bits
+    const int mode = std::fegetround();
+    std::fesetround(FE_TONEAREST);
+    a = std::nearbyint(std::ldexp(pe, k_max));
+    b = std::nearbyint(std::ldexp(qe, k_max));
+    std::fesetround(mode);
+    kk = k_max;
+  }
+  if (k) *k = kk;
+  if (P) *P = (uint64_t)a;
+  if (Q) *Q = (uint64_t)b;
+  return OKZ_OK;
+}
+
+size_t okz_device_bytes(int64_t L) {
+  if (check_L(L) != OKZ_OK) return 0;
+  return layout_for(L).total;
+}
+
+okz_status okz_create_ex(const okz_params *prm, void *dev_buf, size_t bytes, void *stream,
+                         okz_sim **out) {
+  if (!prm || !out) {
+    set_error("null argument");
+    return OKZ_EINVAL;
+  }
+  okz_status st = check_L(prm->L);
+  if (st != OKZ_OK) return st;
+  int32_t k;
+  uint64_t P, Q;
+  st = okz_thresholds(prm->p, prm->q, prm->s_sel, prm->k_max, &k, &P, &Q);
+  if (st != OKZ_OK) return st;
+  int kernel = prm->kernel;
+  if (kernel == OKZ_KERNEL_AUTO)
+    kernel = stream_kernel_supports(prm->L) ? OKZ_KERNEL_STREAM : OKZ_KERNEL_PLAIN;
+  if (kernel == OKZ_KERNEL_STREAM && !stream_kernel_supports(prm->L)) {
+    set_error("the streaming kernel needs L % 4096 == 0 and L <= 131072");
+    return OKZ_EUNSUPPORTED;
+  }
+  if (kernel != OKZ_KERNEL_PLAIN && kernel != OKZ_KERNEL_STREAM) {
+    set_error("unknown kernel selector");
+    return OKZ_EINVAL;
+  }
+  const Layout lay = layout_for(prm->L);
+  if (dev_buf && (bytes < lay.total || ((uintptr_t)dev_buf & 255u))) {
+    set_error("external device buffer too small or not 256-byte aligned");
+    return OKZ_ENOMEM;
+  }
+
+  okz_sim *sim = new (std::nothrow) okz_sim();
+  if (!sim) {
+    set_error("host allocation failed");
+    return OKZ_ENOMEM;
+  }
+  sim->prm = *prm;
+  sim->acc.P = P;
+  sim->acc.Q = Q;
+  sim->acc.k = k;
+  sim->kernel = kernel;
+  sim->lay = lay;
+  sim->t = 0;
+  sim->cur = 0;
+  cudaError_t e = cudaGetDevice(&sim->device);
+  if (e != cudaSuccess) {
+    delete sim;
+    return cuda_fail(e, "cudaGetDevice");
+  }
+  if (stream) {
+    sim->stream = (cudaStream_t)stream;
+    sim->own_stream = false;
+  } else {
+    e = cudaStreamCreateWithFlags(&sim->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      delete sim;
+      return cuda_fail(e, "cudaStreamCreateWithFlags");
+    }
+    sim->own_stream = true;
+  }
+  if (dev_buf) {
+    sim->base = (char *)dev_buf;
+    sim->own_mem = false;
+  } else {
+    e = cudaMalloc((void **)&sim->base, lay.total);
+    if (e != cudaSuccess) {
+      if (sim->own_stream) cudaStreamDestroy(sim->stream);
+      delete sim;
+      cudaGetLastError();
+      set_error("cudaMalloc of " + std::to_string(lay.total) + " bytes failed");
+      return OKZ_ENOMEM;
+    }
+    sim->own_mem = true;
+  }
+  sim->planes[0] = (uint32_t *)(sim->base + lay.off_planes0);
+  sim->planes[1] = (uint32_t *)(sim->base + lay.off_planes1);
+  sim->hcol = (int64_t *)(sim->base + lay.off_hcol);
+  sim->partials = (unsigned long long *)(sim->base + lay.off_partials);
+  sim->ctrl = (Ctrl *)(sim->base + lay.off_ctrl);
+
+  e = cudaMemsetAsync(sim->ctrl, 0, sizeof(Ctrl), sim->stream);
+  if (e == cudaSuccess) e = launch_init_flat(sim->planes[0], prm->L, sim->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(sim->stream);
+  if (e != cudaSuccess) {
+    okz_status r = cuda_fail(e, "initialisation");
+    if (sim->own_mem) cudaFree(sim->base);
+    if (sim->own_stream) cudaStreamDestroy(sim->stream);
+    delete sim;
+    return r;
+  }
+  *out = sim;
+  return OKZ_OK;
+}
+
+okz_status okz_create(int64_t L, double p, double q, uint64_t seed, okz_sim **out) {
+  okz_params prm;
+  okz_params_init(&prm);
+  prm.L = L;
+  prm.p = p;
+  prm.q = q;
+  prm.seed = seed;
+  return okz_create_ex(&prm, nullptr, 0, nullptr, out);
+}
+
+okz_status okz_sweep(okz_sim *sim, int64_t n) {
+  if (!sim || n < 0) {
+    set_error("null simulation or negative sweep count");
+    return OKZ_EINVAL;
+  }
+  if ((uint64_t)n > 0xFFFFFFFFull - sim->t) {
+    set_error("sweep counter would pass 2^32 - 1");
+    return OKZ_EOVERFLOW;
+  }
+  const int64_t L = sim->prm.L;
+  for (int64_t i = 0; i < n; ++i) {
+    const uint32_t t = (uint32_t)sim->t;
+    cudaError_t e;
+    if (sim->kernel == OKZ_KERNEL_STREAM) {
+      e = launch_sweep_stream(sim->planes[sim->cur], sim->planes[1 - sim->cur], L, t,
+                              sim->prm.seed, sim->acc, sim->ctrl, sim->stream);
+      if (e == cudaSuccess) sim->cur = 1 - sim->cur;
+    } else {
+      e = launch_halfsweep_plain(sim->planes[sim->cur], L, 0, t, sim->prm.seed, sim->acc,
+                                 sim->ctrl, sim->stream);
+      if (e == cudaSuccess)
+        e = launch_halfsweep_plain(sim->planes[sim->cur], L, 1, t, sim->prm.seed, sim->acc,
+                                   sim->ctrl, sim->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "sweep launch");
+    sim->t += 1;
+  }
+  return OKZ_OK;
+}
+
+static okz_status sync_and_check(okz_sim *sim) {
+  cudaError_t e = cudaStreamSynchronize(sim->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  unsigned int err = 0;
+  e = cudaMemcpy(&err, &sim->ctrl->err, sizeof(err), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "reading the device error word");
+  if (err & kErrWaitTimeout) {
+    set_error("a bounded device-side wait timed out");
+    return OKZ_ETIMEOUT;
+  }
+  return OKZ_OK;
+}
+
+okz_status okz_synchronize(okz_sim *sim) {
+  if (!sim) {
+    set_error("null simulation");
+    return OKZ_EINVAL;
+  }
+  return sync_and_check(sim);
+}
+
+void *okz_stream(okz_sim *sim) { return sim ? (void *)sim->stream : nullptr; }
+
+// Runs the power-sum kernels and reads back H0 and S_1..S_nmom (about H0).
+static okz_status power_sums(okz_sim *sim, int nmom, long long *H0, __int128 S[4]) {
+  cudaError_t e = launch_power_sums(sim->planes[sim->cur], sim->prm.L, nmom, sim->hcol,
+                                    sim->partials, sim->ctrl, sim->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "power-sum launch");
+  okz_status st = sync_and_check(sim);
+  if (st != OKZ_OK) return st;
+  Ctrl c;
+  e = cudaMemcpy(&c, sim->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "reading the sums");
+  *H0 = c.H0;
+  for (int n = 0; n < 4; ++n)
+    S[n] = (__int128)(((unsigned __int128)c.sum[2 * n + 1] << 64) |
+                      (unsigned __int128)c.sum[2 * n]);
+  return OKZ_OK;
+}
+
+okz_status okz_width2(okz_sim *sim, okz_i128 *S1, okz_i128 *S2, double *W2) {
+  if (!sim) {
+    set_error("null simulation");
+    return OKZ_EINVAL;
+  }
+  long long H0 = 0;
+  __int128 S[4];
+  okz_status st = power_sums(sim, 2, &H0, S);
+  if (st != OKZ_OK) return st;
+  const __int128 N = (__int128)sim->prm.L * sim->prm.L;
+  // W^2 = (N S2 - S1^2) / N^2 with sums about H0 (the numerator is shift-free)
+  const __int128 num = N * S[1] - S[0] * S[0];
+  const double w2 = (double)num / ((double)N * (double)N);
+  // absolute sums: sum h = S1c + N H0, sum h^2 = S2c + 2 H0 S1c + N H0^2
+  const __int128 h0 = H0;
+  if (S1) *S1 = from_i128(S[0] + N * h0);
+  if (S2) *S2 = from_i128(S[1] + 2 * h0 * S[0] + N * h0 * h0);
+  if (W2) *W2 = w2;
+  return OKZ_OK;
+}
+
+okz_status okz_moments(okz_sim *sim, okz_i128 Sk[4], double *W2, double *skew,
+                       double *kurt) {
+  if (!sim) {
+    set_error("null simulation");
+    return OKZ_EINVAL;
+  }
+  if (sim->prm.L > 131072) {
+    set_error("okz_moments needs L <= 131072");
+    return OKZ_EUNSUPPORTED;
+  }
+  long long H0 = 0;
+  __int128 S[4];
+  okz_status st = power_sums(sim, 4, &H0, S);
+  if (st != OKZ_OK) return st;
+  const __int128 N = (__int128)sim->prm.L * sim->prm.L;
+  if (Sk)
+    for (int n = 0; n < 4; ++n) Sk[n] = from_i128(S[n]);
+  if (W2) *W2 = (double)(N * S[1] - S[0] * S[0]) / ((double)N * (double)N);
+  const long double n_ = (long double)N;
+  const long double mu = (long double)S[0] / n_;
+  const long double a2 = (long double)S[1] / n_, a3 = (long double)S[2] / n_,
+                    a4 = (long double)S[3] / n_;
+  const long double m2 = a2 - mu * mu;
+  const long double m3 = a3 - 3.0L * mu * a2 + 2.0L * mu * mu * mu;
+  const long double m4 = a4 - 4.0L * mu * a3 + 6.0L * mu * mu * a2 - 3.0L * mu * mu * mu * mu;
+  if (skew) *skew = (double)(m3 / powl(m2, 1.5L));
+  if (kurt) *kurt = (double)(m4 / (m2 * m2) - 3.0L);
+  return OKZ_OK;
+}
+
+okz_status okz_heights(okz_sim *sim, int64_t y0, int64_t ny, int32_t *out,
+                       int out_is_device) {
+  if (!sim || !out || y0 < 0 || ny < 0 || y0 + ny > sim->prm.L) {
+    set_error("bad heights request");
+    return OKZ_EINVAL;
+  }
+  if (ny == 0) return OKZ_OK;
+  const int64_t L = sim->prm.L;
+  const size_t bytes = (size_t)ny * (size_t)L * sizeof(int32_t);
+  int32_t *dst = out;
+  cudaError_t e;
+  if (!out_is_device) {
+    e = cudaMallocAsync((void **)&dst, bytes, sim->stream);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      set_error("device staging allocation for heights failed");
+      return OKZ_ENOMEM;
+    }
+  }
+  unsigned int zero = 0;
+  e = cudaMemcpyAsync(&sim->ctrl->err, &zero, sizeof(zero), cudaMemcpyHostToDevice,
+                      sim->stream);
+  if (e == cudaSuccess)
+    e = launch_heights(sim->planes[sim->cur], L, y0, ny, sim->hcol, dst, sim->ctrl,
+                       sim->stream);
+  if (e == cudaSuccess && !out_is_device)
+    e = cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, sim->stream);
+  if (!out_is_device) cudaFreeAsync(dst, sim->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "heights");
+  e = cudaStreamSynchronize(sim->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "heights synchronize");
+  unsigned int err = 0;
+  e = cudaMemcpy(&err, &sim->ctrl->err, sizeof(err), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "heights error word");
+  if (err & kErrHeightRange) {
+    set_error("a height does not fit in int32");
+    return OKZ_EOVERFLOW;
+  }
+  return OKZ_OK;
+}
+
+okz_status okz_state(okz_sim *sim, uint32_t *planes_out, int out_is_device, int64_t *H0,
+                     uint64_t *t) {
+  if (!sim) {
+    set_error("null simulation");
+    return OKZ_EINVAL;
+  }
+  cudaError_t e = cudaSuccess;
+  if (planes_out)
+    e = cudaMemcpyAsync(planes_out, sim->planes[sim->cur], sim->lay.planes_bytes,
+                        out_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                        sim->stream);
+  long long h0 = 0;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&h0, &sim->ctrl->H0, sizeof(h0), cudaMemcpyDeviceToHost, sim->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "state copy");
+  okz_status st = sync_and_check(sim);
+  if (st != OKZ_OK) return st;
+  if (H0) *H0 = h0;
+  if (t) *t = sim->t;
+  return OKZ_OK;
+}
+
+okz_status okz_restore(okz_sim *sim, const uint32_t *planes, int in_is_device, int64_t H0,
+                       uint64_t t) {
+  if (!sim || !planes || t > 0xFFFFFFFFull) {
+    set_error("bad restore request");
+    return OKZ_EINVAL;
+  }
+  long long h0 = H0;
+  cudaError_t e = cudaMemcpyAsync(sim->planes[sim->cur], planes, sim->lay.planes_bytes,
+                                  in_is_device ? cudaMemcpyDeviceToDevice
+                                               : cudaMemcpyHostToDevice,
+                                  sim->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&sim->ctrl->H0, &h0, sizeof(h0), cudaMemcpyHostToDevice, sim->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "restore copy");
+  e = cudaStreamSynchronize(sim->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "restore synchronize");
+  sim->t = t;
+  return OKZ_OK;
+}
+
+okz_status okz_get_info(okz_sim *sim, okz_info *info) {
+  if (!sim || !info) {
+    set_error("null argument");
+    return OKZ_EINVAL;
+  }
+  int64_t H0 = 0;
+  okz_status st = okz_state(sim, nullptr, 0, &H0, nullptr);
+  if (st != OKZ_OK) return st;
+  info->L = sim->prm.L;
+  info->t = sim->t;
+  info->H0 = H0;
+  info->k = sim->acc.k;
+  info->kernel = sim->kernel;
+  info->P = sim->acc.P;
+  info->Q = sim->acc.Q;
+  info->device_bytes = sim->lay.total;
+  return OKZ_OK;
+}
+
+okz_status okz_destroy(okz_sim *sim) {
+  if (!sim) return OKZ_OK;
+  cudaError_t e = cudaStreamSynchronize(sim->stream);
+  if (sim->own_mem) cudaFree(sim->base);
+  if (sim->own_stream) cudaStreamDestroy(sim->stream);
+  delete sim;
+  if (e != cudaSuccess) return cuda_fail(e, "destroy synchronize");
+  return OKZ_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,45 @@
+// okz_internal.h -- host-side declarations shared by the library's .cu files.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+
+#include "../../include/okz.h"
+#include "okz_device.cuh"
+
+namespace okz {
+
+// Upper bound on the blocks of the row-reduction kernel; its per-block
+// partial sums live in the simulation's device buffer.
+constexpr int kMaxReduceBlocks = 2048;
+
+struct Layout {
+  size_t planes_bytes;  // one state buffer: X plane then Y plane
+  size_t off_planes0, off_planes1, off_hcol, off_partials, off_ctrl, total;
+};
+Layout layout_for(int64_t L);
+
+void set_error(const std::string &msg);
+okz_status cuda_fail(cudaError_t e, const char *what);
+
+// ---- launchers (each returns cudaGetLastError() of its launches) ----------
+cudaError_t launch_init_flat(uint32_t *planes, int64_t L, cudaStream_t st);
+cudaError_t launch_halfsweep_plain(uint32_t *planes, int64_t L, int s, uint32_t t,
+                                   uint64_t seed, const Accept &acc, Ctrl *ctrl,
+                                   cudaStream_t st);
+bool stream_kernel_supports(int64_t L);
+cudaError_t launch_sweep_stream(const uint32_t *src, uint32_t *dst, int64_t L,
+                                uint32_t t, uint64_t seed, const Accept &acc,
+                                Ctrl *ctrl, cudaStream_t st);
+// Measurement: column heights, then exact power sums about H0 into ctrl->sum.
+// nmom = 2 (S1, S2) or 4 (S1..S4).
+cudaError_t launch_power_sums(const uint32_t *planes, int64_t L, int nmom,
+                              int64_t *hcol, unsigned long long *partials,
+                              Ctrl *ctrl, cudaStream_t st);
+cudaError_t launch_heights(const uint32_t *planes, int64_t L, int64_t y0, int64_t ny,
+                           int64_t *hcol, int32_t *out, Ctrl *ctrl, cudaStream_t st);
+
+}  // namespace okz

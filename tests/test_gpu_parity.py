@@ -1,0 +1,306 @@
+"""GPU parity: the CUDA path through the C-ABI against the CPU oracle.
+
+Integer state (bond planes, H0, t, exact sums) must match bit for bit; W^2
+is finalized from exact integers on both sides and must be equal as doubles;
+skewness and kurtosis (long-double finalization) agree to 1e-12 relative.
+"""
+import os
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def okz():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1110_6745_gb300 import _build
+    _build.build()
+    import paper_1110_6745_gb300 as m
+    m.lib()
+    return m
+
+
+def _compare(sim, ref):
+    planes, H0, t = sim.state()
+    Xw, Yw = ref.packed()
+    assert np.array_equal(planes[0], Xw), "X plane differs"
+    assert np.array_equal(planes[1], Yw), "Y plane differs"
+    assert (H0, t) == (ref.H0, ref.t)
+
+
+MODES = [  # p, q, s_sel: k and kernel path
+    (1.0, 0.0, 0.5),     # k = 1, only minima move (the growth workloads)
+    (0.75, 0.25, 0.5),   # k = 3
+    (1.0, 1.0, 0.5),     # k = 1, minima and maxima
+    (0.95, 0.05, 0.5),   # k = 32, rounded thresholds
+    (1.0, 0.0, 1.0),     # k = 0, deterministic growth
+    (0.0, 1.0, 1.0),     # k = 0, deterministic etching
+    (0.5, 0.5, 0.5),     # k = 2
+]
+
+
+@pytest.mark.parametrize("L", [32, 64, 96, 128, 256, 480])
+@pytest.mark.parametrize("p,q,s_sel", MODES)
+def test_plain_kernel_matches_oracle(okz, orc, L, p, q, s_sel):
+    seed = 1000 + L
+    ref = orc.Sim(L, p, q, seed, s_sel=s_sel)
+    with okz.Simulation(L, p, q, seed=seed, s_sel=s_sel, kernel=okz.OKZ_KERNEL_PLAIN) as sim:
+        for n in (1, 2, 7):
+            ref.sweep(n)
+            sim.sweep(n)
+            _compare(sim, ref)
+            S1, S2, W2 = sim.width2()
+            assert (S1, S2) == ref.sums() and W2 == ref.width2()
+
+
+@pytest.mark.parametrize("L", [4096, 12288])
+@pytest.mark.parametrize("p,q,s_sel", MODES)
+def test_stream_kernel_matches_oracle(okz, orc, L, p, q, s_sel):
+    seed = 77 + L
+    ref = orc.Sim(L, p, q, seed, s_sel=s_sel)
+    with okz.Simulation(L, p, q, seed=seed, s_sel=s_sel, kernel=okz.OKZ_KERNEL_STREAM) as sim:
+        for n in (1, 3):
+            ref.sweep(n)
+            sim.sweep(n)
+            _compare(sim, ref)
+        S1, S2, W2 = sim.width2()
+        assert (S1, S2) == ref.sums() and W2 == ref.width2()
+
+
+@pytest.mark.parametrize("L", [4096, 8192, 16384])
+def test_stream_equals_plain_long_run(okz, L):
+    """Both kernels give identical lattices over many sweeps (no oracle needed)."""
+    a = okz.Simulation(L, 0.75, 0.25, seed=5, kernel=okz.OKZ_KERNEL_STREAM)
+    b = okz.Simulation(L, 0.75, 0.25, seed=5, kernel=okz.OKZ_KERNEL_PLAIN)
+    for n in (10, 40):
+        a.sweep(n)
+        b.sweep(n)
+        pa, ha, ta = a.state()
+        pb, hb, tb = b.state()
+        assert np.array_equal(pa, pb) and (ha, ta) == (hb, tb)
+        assert a.width2() == b.width2()
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("L,kernel", [(64, 1), (256, 1), (4096, 2)])
+def test_moments_and_heights_match_oracle(okz, orc, L, kernel):
+    ref = orc.Sim(L, 0.95, 0.05, 3)
+    with okz.Simulation(L, 0.95, 0.05, seed=3, kernel=kernel) as sim:
+        ref.sweep(25)
+        sim.sweep(25)
+        Sk, W2, sk, ku = sim.moments()
+        assert Sk == ref.power_sums()
+        assert W2 == ref.width2()
+        rsk, rku = ref.skew_kurt()
+        assert sk == pytest.approx(rsk, rel=1e-12, abs=1e-15)
+        assert ku == pytest.approx(rku, rel=1e-12, abs=1e-15)
+        h = ref.heights()
+        assert np.array_equal(sim.heights(), h)
+        assert np.array_equal(sim.heights(y0=L // 2 - 3, ny=5), h[L // 2 - 3:L // 2 + 2])
+
+
+def test_flat_start_width(okz):
+    for L in (32, 256, 4096):
+        with okz.Simulation(L, 1.0, 0.0, seed=1) as sim:
+            S1, S2, W2 = sim.width2()
+            assert W2 == 0.25 and S1 == L * L // 2 and S2 == L * L // 2
+
+
+def test_growth_series_L256(okz, orc):
+    """L = 256, p = 1, q = 0, seed 1, 1000 sweeps, W^2 at 20 log-spaced times:
+    every record equal to the oracle's."""
+    times = orc.sample_times(1000, 20)
+    ref = orc.Sim(256, 1.0, 0.0, 1)
+    with okz.Simulation(256, 1.0, 0.0, seed=1) as sim:
+        for t in times:
+            ref.sweep(t - ref.t)
+            sim.sweep(t - sim.info().t)
+            S1, S2, W2 = sim.width2()
+            assert (S1, S2) == ref.sums() and W2 == ref.width2(), t
+            assert sim.info().H0 == ref.H0
+        _compare(sim, ref)
+
+
+def test_checkpoint_resume_is_exact(okz):
+    for L, kernel in [(256, 1), (8192, 2)]:
+        a = okz.Simulation(L, 0.75, 0.25, seed=9, kernel=kernel)
+        a.sweep(30)
+        planes, H0, t = a.state()
+        a.sweep(30)
+        b = okz.Simulation(L, 0.75, 0.25, seed=9, kernel=kernel)
+        b.restore(planes, H0, t)
+        b.sweep(30)
+        pa, ha, ta = a.state()
+        pb, hb, tb = b.state()
+        assert np.array_equal(pa, pb) and (ha, ta) == (hb, tb) == (ha, 60)
+        a.close()
+        b.close()
+
+
+def test_torch_buffer_and_stream(okz):
+    import torch
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        a = okz.Simulation(4096, 1.0, 0.0, seed=4, torch_buffer=True)
+    assert a.stream == s.cuda_stream
+    b = okz.Simulation(4096, 1.0, 0.0, seed=4)
+    a.sweep(12)
+    b.sweep(12)
+    assert np.array_equal(a.state()[0], b.state()[0])
+    # device-side state and heights outputs
+    dev = torch.empty(2 * 4096 * 4096 // 32, dtype=torch.int32, device="cuda")
+    a.state(out=dev)
+    assert np.array_equal(dev.cpu().numpy().view(np.uint32).reshape(2, 4096, 128),
+                          b.state()[0])
+    hd = torch.empty(3 * 4096, dtype=torch.int32, device="cuda")
+    a.heights(y0=100, ny=3, out=hd)
+    assert np.array_equal(hd.cpu().numpy().reshape(3, 4096), b.heights(y0=100, ny=3))
+    a.close()
+    b.close()
+
+
+def test_sweep_counter_overflow(okz):
+    with okz.Simulation(64, 1.0, 0.0, seed=1) as sim:
+        planes, H0, _ = sim.state()
+        sim.restore(planes, H0, 2**32 - 2)
+        sim.sweep(1)
+        with pytest.raises(okz.OkzError) as e:
+            sim.sweep(1)
+        assert e.value.status == okz.OKZ_EOVERFLOW
+
+
+def test_exact_sums_beyond_64_bits(okz, orc):
+    """A surface lifted by 2^40: S2 ~ 2^92 stays exact (128-bit)."""
+    ref = orc.Sim(64, 0.75, 0.25, 2)
+    ref.sweep(9)
+    with okz.Simulation(64, 0.75, 0.25, seed=2) as sim:
+        sim.sweep(9)
+        planes, H0, t = sim.state()
+        sim.restore(planes, H0 + 2**40, t)
+        ref.H0 += 2**40
+        S1, S2, W2 = sim.width2()
+        assert (S1, S2) == ref.sums() and S2 > 2**64
+        assert W2 == ref.width2()
+        with pytest.raises(okz.OkzError) as e:
+            sim.heights()
+        assert e.value.status == okz.OKZ_EOVERFLOW
+
+
+# --------------------------------------------------------------------------
+# Full-size checks at L = 2^17 (16 GiB lattice state pair on the device)
+# --------------------------------------------------------------------------
+def _unpack_window(planes_dev, L, x0, y0, w, h):
+    """Bits of a w x h window (with periodic wrap) from device planes (2, L, L/32)."""
+    import torch
+    rows = (torch.arange(h, device=planes_dev.device) + y0) % L
+    xs = (torch.arange(w, device=planes_dev.device) + x0) % L
+    out = []
+    for plane in (0, 1):
+        words = planes_dev[plane][rows][:, xs // 32]
+        bits = (words >> (xs % 32).to(torch.int32)) & 1
+        out.append(bits.to(torch.uint8).cpu().numpy())
+    return out
+
+
+def _invariants_on_device(planes_dev, L):
+    """Every row of sigma_x and every column of sigma_y sums to zero, and the
+    curl vanishes on every plaquette (bitwise, on the device)."""
+    import torch
+    Xp, Yp = planes_dev[0], planes_dev[1]
+    lut = torch.tensor([bin(i).count("1") for i in range(256)], dtype=torch.int64,
+                       device=planes_dev.device)
+    colsum = torch.zeros(L, dtype=torch.int64, device=planes_dev.device)
+    chunk = 1024
+    for y0 in range(0, L, chunk):
+        xs = Xp[y0:y0 + chunk]
+        ones = lut[xs.contiguous().view(torch.uint8).long()].view(xs.shape[0], -1).sum(1)
+        assert bool((ones == L // 2).all()), "row of sigma_x does not sum to 0"
+        ys = Yp[y0:y0 + chunk]
+        for b in range(32):
+            colsum[b::32] += ((ys >> b) & 1).sum(0)
+        # curl: X(x,y) + Y(x+1,y) == Y(x,y) + X(x,y+1), as bits
+        yn = torch.roll(ys, shifts=-1, dims=1)
+        yr = ((ys >> 1) & 0x7FFFFFFF) | ((yn & 1) << 31)  # Y(x+1, y)
+        xu = Xp[(torch.arange(y0, y0 + xs.shape[0], device=xs.device) + 1) % L]
+        a, c = xs, ys
+        assert bool((((a ^ yr) == (c ^ xu)) & ((a & yr) == (c & xu))).all()), "curl"
+    assert bool((colsum == L // 2).all()), "column of sigma_y does not sum to 0"
+
+
+def test_full_size_L131072(okz, orc):
+    """The headline lattice in the benchmark's launch configuration: windows
+    checked site by site against the oracle's light-cone simulation, global
+    invariants on the device, sampled heights against Eq. (3) evaluated by
+    the oracle, and the exact sums against an independent chunked reduction."""
+    import torch
+    L, n, seed = 1 << 17, 8, 11
+    with okz.Simulation(L, 1.0, 0.0, seed=seed) as sim:
+        assert sim.info().kernel == okz.OKZ_KERNEL_STREAM
+        sim.sweep(n)
+        planes = torch.empty((2, L, L // 32), dtype=torch.int32, device="cuda")
+        _, H0, t = sim.state(out=planes)
+        assert t == n
+        m = 2 * n + 2
+        for (x0, y0) in [(1000, 2000), (L - 40, L - 40), (70000, 862 - 60), (0, 0),
+                         (L - 150, 5000)]:
+            w = h = 160
+            WX, WY = orc.window_flat_sweeps(L, x0, y0, w, h, 1.0, 0.0, seed, n)
+            GX, GY = _unpack_window(planes, L, x0, y0, w, h)
+            assert np.array_equal(GX[m:h - m, m:w - m], WX[m:h - m, m:w - m]), (x0, y0)
+            assert np.array_equal(GY[m:h - m, m:w - m], WY[m:h - m, m:w - m]), (x0, y0)
+        _invariants_on_device(planes, L)
+        # sampled heights against the oracle's path sum on the host copy
+        host = planes.cpu().numpy().view(np.uint32)
+        for y in (0, 1, 863, 65536, L - 1):
+            row = sim.heights(y0=y, ny=1)[0]
+            for x in (0, 1, 31, 32, 4095, 4096, 99999, L - 1):
+                assert row[x] == orc.height_packed(L, host[0], host[1], H0, x, y), (x, y)
+        # exact sums against a chunked reduction of the materialised heights
+        S1, S2, W2 = sim.width2()
+        s1 = s2 = 0
+        buf = torch.empty((2048, L), dtype=torch.int32, device="cuda")
+        for y0 in range(0, L, 2048):
+            sim.heights(y0=y0, ny=2048, out=buf)
+            hh = buf.long()
+            s1 += int(hh.sum())
+            s2 += int((hh * hh).sum())
+        assert (S1, S2) == (s1, s2)
+        N = L * L
+        assert W2 == float(N * s2 - s1 * s1) / (float(N) * float(N)) or \
+            W2 == pytest.approx((N * s2 - s1 * s1) / N / N, rel=1e-15)
+
+
+def _golden_rows(path):
+    rows, digest = [], None
+    for line in open(path):
+        if line.startswith("# final_planes_sha256"):
+            digest = line.split()[-1]
+        elif line.strip() and not line.startswith("#"):
+            t, H0, S1, S2, W2 = line.split()
+            rows.append((int(t), int(H0), int(S1), int(S2), float(W2)))
+    return rows, digest
+
+
+def test_growth_series_L16384_golden(okz):
+    """L = 2^14, p = 1, q = 0, seed 7, 10^4 sweeps, 40 log-spaced samples:
+    every (t, H0, S1, S2, W^2) record and the final planes equal the oracle's
+    stored run (tests/golden/make_growth_golden.py)."""
+    import hashlib
+    path = os.path.join(GOLDEN, "growth_L16384_p1_q0_seed7.txt")
+    if not os.path.exists(path):
+        pytest.fail("golden series missing: run tests/golden/make_growth_golden.py")
+    rows, digest = _golden_rows(path)
+    with okz.Simulation(16384, 1.0, 0.0, seed=7) as sim:
+        assert sim.info().kernel == okz.OKZ_KERNEL_STREAM
+        for (t, H0, S1, S2, W2) in rows:
+            sim.sweep(t - sim.info().t)
+            s1, s2, w2 = sim.width2()
+            assert (sim.info().t, sim.info().H0, s1, s2, w2) == (t, H0, S1, S2, W2)
+        planes, _, _ = sim.state()
+        assert hashlib.sha256(planes.tobytes()).hexdigest() == digest
