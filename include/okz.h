@@ -87,6 +87,8 @@ typedef struct okz_params {
     double s_sel;   /* selection probability of an active site, (0, 1]; 0.5      */
     int32_t k_max;  /* largest acceptance precision in bits, 1..32; 32            */
     int32_t kernel; /* OKZ_KERNEL_*                                                */
+    int32_t words_per_thread; /* STREAM: 4 or 8 words of 32 sites per thread; 0 = auto */
+    int32_t sweeps_per_pass;  /* STREAM: 1 or 2 sweeps fused per launch; 0 = auto      */
 } okz_params;
 
 typedef struct okz_info {
@@ -102,7 +104,9 @@ typedef struct okz_info {
 typedef struct okz_sim okz_sim;
 
 /* Fills *prm with the defaults: L = 0, p = 1, q = 0, seed = 0, s_sel = 0.5,
- * k_max = 32, kernel = AUTO. */
+ * k_max = 32, kernel = AUTO, words_per_thread = 0, sweeps_per_pass = 0. The
+ * last two only choose how the stream kernel tiles the work; results are
+ * bit-identical for every choice. */
 void okz_params_init(okz_params *prm);
 
 /* Device bytes a simulation of size L needs when memory is passed to

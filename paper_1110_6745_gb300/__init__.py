@@ -39,7 +39,8 @@ class okz_i128(ctypes.Structure):
 class okz_params(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int64), ("p", ctypes.c_double), ("q", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("s_sel", ctypes.c_double),
-                ("k_max", ctypes.c_int32), ("kernel", ctypes.c_int32)]
+                ("k_max", ctypes.c_int32), ("kernel", ctypes.c_int32),
+                ("words_per_thread", ctypes.c_int32), ("sweeps_per_pass", ctypes.c_int32)]
 
 
 class okz_info(ctypes.Structure):
@@ -105,11 +106,13 @@ def okz_last_error():
     return lib().okz_last_error().decode()
 
 
-def okz_params_init(L=0, p=1.0, q=0.0, seed=0, s_sel=0.5, k_max=32, kernel=OKZ_KERNEL_AUTO):
+def okz_params_init(L=0, p=1.0, q=0.0, seed=0, s_sel=0.5, k_max=32, kernel=OKZ_KERNEL_AUTO,
+                    words_per_thread=0, sweeps_per_pass=0):
     prm = okz_params()
     lib().okz_params_init(ctypes.byref(prm))
     prm.L, prm.p, prm.q, prm.seed = int(L), float(p), float(q), int(seed)
     prm.s_sel, prm.k_max, prm.kernel = float(s_sel), int(k_max), int(kernel)
+    prm.words_per_thread, prm.sweeps_per_pass = int(words_per_thread), int(sweeps_per_pass)
     return prm
 
 
@@ -224,10 +227,12 @@ class Simulation:
     """Owning wrapper: a simulation handle plus the torch buffer it may live in."""
 
     def __init__(self, L, p=1.0, q=0.0, seed=0, s_sel=0.5, k_max=32,
-                 kernel=OKZ_KERNEL_AUTO, torch_buffer=False, stream=None):
+                 kernel=OKZ_KERNEL_AUTO, torch_buffer=False, stream=None,
+                 words_per_thread=0, sweeps_per_pass=0):
         self.L = int(L)
         self._buf = None
-        prm = okz_params_init(L, p, q, seed, s_sel, k_max, kernel)
+        prm = okz_params_init(L, p, q, seed, s_sel, k_max, kernel, words_per_thread,
+                              sweeps_per_pass)
         if torch_buffer:
             import torch
             nbytes = okz_device_bytes(L)

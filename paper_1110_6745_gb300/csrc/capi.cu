@@ -15,6 +15,8 @@ struct okz_sim {
   okz_params prm;
   okz::Accept acc;
   int kernel;
+  int wpt;   // stream kernel: words per thread
+  int fuse;  // stream kernel: sweeps per launch
   int device;
   cudaStream_t stream;
   bool own_stream;
@@ -97,6 +99,8 @@ void okz_params_init(okz_params *prm) {
   prm->s_sel = 0.5;
   prm->k_max = 32;
   prm->kernel = OKZ_KERNEL_AUTO;
+  prm->words_per_thread = 0;
+  prm->sweeps_per_pass = 0;
 }
 
 okz_status okz_thresholds(double p, double q, double s_sel, int32_t k_max, int32_t *k,
@@ -162,6 +166,19 @@ okz_status okz_create_ex(const okz_params *prm, void *dev_buf, size_t bytes, voi
     set_error("unknown kernel selector");
     return OKZ_EINVAL;
   }
+  int wpt = prm->words_per_thread, fuse = prm->sweeps_per_pass;
+  if (kernel == OKZ_KERNEL_STREAM) {
+    if (wpt == 0) wpt = stream_wpt_valid(prm->L, 8) ? 8 : 4;
+    if (fuse == 0) fuse = 1;
+    if (!stream_wpt_valid(prm->L, wpt) || (fuse != 1 && fuse != 2)) {
+      set_error("words_per_thread must be 4 or 8 (8 needs L % 8192 == 0) and "
+                "sweeps_per_pass 1 or 2");
+      return OKZ_EINVAL;
+    }
+  } else {
+    wpt = 0;
+    fuse = 1;
+  }
   const Layout lay = layout_for(prm->L);
   if (dev_buf && (bytes < lay.total || ((uintptr_t)dev_buf & 255u))) {
     set_error("external device buffer too small or not 256-byte aligned");
@@ -178,6 +195,8 @@ okz_status okz_create_ex(const okz_params *prm, void *dev_buf, size_t bytes, voi
   sim->acc.Q = Q;
   sim->acc.k = k;
   sim->kernel = kernel;
+  sim->wpt = wpt;
+  sim->fuse = fuse;
   sim->lay = lay;
   sim->t = 0;
   sim->cur = 0;
@@ -251,12 +270,16 @@ okz_status okz_sweep(okz_sim *sim, int64_t n) {
     return OKZ_EOVERFLOW;
   }
   const int64_t L = sim->prm.L;
-  for (int64_t i = 0; i < n; ++i) {
+  int64_t done = 0;
+  while (done < n) {
     const uint32_t t = (uint32_t)sim->t;
     cudaError_t e;
+    int64_t step = 1;
     if (sim->kernel == OKZ_KERNEL_STREAM) {
+      step = (sim->fuse == 2 && n - done >= 2) ? 2 : 1;
       e = launch_sweep_stream(sim->planes[sim->cur], sim->planes[1 - sim->cur], L, t,
-                              sim->prm.seed, sim->acc, sim->ctrl, sim->stream);
+                              sim->prm.seed, sim->acc, sim->wpt, (int)step, sim->ctrl,
+                              sim->stream);
       if (e == cudaSuccess) sim->cur = 1 - sim->cur;
     } else {
       e = launch_halfsweep_plain(sim->planes[sim->cur], L, 0, t, sim->prm.seed, sim->acc,
@@ -266,7 +289,8 @@ okz_status okz_sweep(okz_sim *sim, int64_t n) {
                                    sim->ctrl, sim->stream);
     }
     if (e != cudaSuccess) return cuda_fail(e, "sweep launch");
-    sim->t += 1;
+    sim->t += (uint64_t)step;
+    done += step;
   }
   return OKZ_OK;
 }

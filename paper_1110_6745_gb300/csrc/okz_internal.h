@@ -31,9 +31,12 @@ cudaError_t launch_halfsweep_plain(uint32_t *planes, int64_t L, int s, uint32_t 
                                    uint64_t seed, const Accept &acc, Ctrl *ctrl,
                                    cudaStream_t st);
 bool stream_kernel_supports(int64_t L);
+// Words per thread the stream kernel can use for L (4 or 8; 0 = not valid).
+bool stream_wpt_valid(int64_t L, int wpt);
+// Runs `fuse` (1 or 2) sweeps t, t+1, .. in one pass from src to dst.
 cudaError_t launch_sweep_stream(const uint32_t *src, uint32_t *dst, int64_t L,
                                 uint32_t t, uint64_t seed, const Accept &acc,
-                                Ctrl *ctrl, cudaStream_t st);
+                                int wpt, int fuse, Ctrl *ctrl, cudaStream_t st);
 // Measurement: column heights, then exact power sums about H0 into ctrl->sum.
 // nmom = 2 (S1, S2) or 4 (S1..S4).
 cudaError_t launch_power_sums(const uint32_t *planes, int64_t L, int nmom,

@@ -72,6 +72,40 @@ def test_stream_kernel_matches_oracle(okz, orc, L, p, q, s_sel):
         assert (S1, S2) == ref.sums() and W2 == ref.width2()
 
 
+@pytest.mark.parametrize("wpt,fuse", [(4, 1), (8, 1), (4, 2), (8, 2)])
+@pytest.mark.parametrize("p,q,s_sel", [(1.0, 0.0, 0.5), (0.75, 0.25, 0.5), (1.0, 1.0, 0.5),
+                                       (0.95, 0.05, 0.5)])
+def test_stream_variants_match_oracle(okz, orc, wpt, fuse, p, q, s_sel):
+    """Every tiling (words per thread) and temporal-blocking depth (sweeps per
+    launch) gives the oracle's lattice, including odd sweep counts."""
+    L, seed = 8192, 31
+    ref = orc.Sim(L, p, q, seed, s_sel=s_sel)
+    with okz.Simulation(L, p, q, seed=seed, s_sel=s_sel, kernel=okz.OKZ_KERNEL_STREAM,
+                        words_per_thread=wpt, sweeps_per_pass=fuse) as sim:
+        for n in (1, 2, 3):
+            ref.sweep(n)
+            sim.sweep(n)
+            _compare(sim, ref)
+        S1, S2, W2 = sim.width2()
+        assert (S1, S2) == ref.sums() and W2 == ref.width2()
+
+
+@pytest.mark.parametrize("wpt,fuse", [(4, 2), (8, 2), (8, 1)])
+def test_stream_variants_long_run_L32768(okz, wpt, fuse):
+    """Long runs at L = 2^15 (several CTA bands per SM) agree with the plain kernel."""
+    L = 32768
+    a = okz.Simulation(L, 1.0, 0.0, seed=8, kernel=okz.OKZ_KERNEL_STREAM,
+                       words_per_thread=wpt, sweeps_per_pass=fuse)
+    b = okz.Simulation(L, 1.0, 0.0, seed=8, kernel=okz.OKZ_KERNEL_PLAIN)
+    a.sweep(37)
+    b.sweep(37)
+    pa, ha, ta = a.state()
+    pb, hb, tb = b.state()
+    assert np.array_equal(pa, pb) and (ha, ta) == (hb, tb)
+    a.close()
+    b.close()
+
+
 @pytest.mark.parametrize("L", [4096, 8192, 16384])
 def test_stream_equals_plain_long_run(okz, L):
     """Both kernels give identical lattices over many sweeps (no oracle needed)."""
