@@ -32,7 +32,9 @@ SEED = 11
 SWEEPS_PER_STEP = 256
 METRIC = "site-update attempts/s (GUPS)"
 UNIT = "GUPS (1e9 site-update attempts/s)"
-BYTES_PER_SITE_SWEEP = 0.5  # read 2 bits + write 2 bits per site, one pass
+# algorithmic bytes per site per launch: read + write every stored bit once
+BYTES_PER_SITE_LAUNCH = {"slope": 0.5, "parity": 0.25}
+KERNELS = {"auto": 0, "slope": 2, "parity": 4}
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one sweep-kernel launch, taken
 # by ncu on an L = 32768 lattice and scaled by the site count to L = 2^17, for
@@ -195,8 +197,14 @@ def run_gpu(args, world, rank, local):
     N = L * L
     stream = torch.cuda.Stream(device=dev)
     with torch.cuda.stream(stream):
-        sim = okz.Simulation(L, 1.0, 0.0, seed=SEED + rank, torch_buffer=True)
-    assert sim.info().kernel == okz.OKZ_KERNEL_STREAM
+        sim = okz.Simulation(L, 1.0, 0.0, seed=SEED + rank, torch_buffer=True,
+                             kernel=KERNELS[args.kernel], words_per_thread=args.wpt,
+                             sweeps_per_pass=args.fuse)
+    kind = sim.info().kernel
+    assert kind in (okz.OKZ_KERNEL_STREAM, okz.OKZ_KERNEL_PARITY_STREAM)
+    repr_name = "parity" if kind == okz.OKZ_KERNEL_PARITY_STREAM else "slope"
+    fuse = sim.fuse
+    wpt = sim.wpt
     # checkpoint of the striped start, kept on the device
     start_planes = torch.empty(2 * L * L // 32, dtype=torch.int32, device=dev)
     sim.state(out=start_planes)
@@ -234,11 +242,12 @@ def run_gpu(args, world, rank, local):
     elapsed_ms = _max_over_ranks(world, elapsed_ms, dev)
     sweeps = SWEEPS_PER_STEP * args.steps
     value = world * N * sweeps / (elapsed_ms / 1e3) / 1e9
-    launches = args.steps * (SWEEPS_PER_STEP + 3)  # sweeps + 3 measurement kernels
+    sweep_launches = SWEEPS_PER_STEP // fuse
+    launches = args.steps * (sweep_launches + 3)  # sweep launches + 3 measurement kernels
 
     # roofline of the sweep kernel: algorithmic bytes per launch / launch time
-    per_launch_s = sweep_ms / 1e3 / sweeps
-    alg_bytes = BYTES_PER_SITE_SWEEP * N
+    per_launch_s = sweep_ms / 1e3 / (args.steps * sweep_launches)
+    alg_bytes = BYTES_PER_SITE_LAUNCH[repr_name] * N
     achieved = alg_bytes / per_launch_s / 1e9
     peak, peak_kind = _peaks()
     traffic = None
@@ -279,10 +288,13 @@ def run_gpu(args, world, rank, local):
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "sweep_stream_kernel", "peak_kind": peak_kind,
-                     "bytes_per_launch": alg_bytes,
+                     "kernel": ("parity_stream_kernel" if repr_name == "parity"
+                                else "sweep_stream_kernel"),
+                     "peak_kind": peak_kind, "bytes_per_launch": alg_bytes,
+                     "sweeps_per_launch": fuse, "words_per_thread": wpt,
                      "launch_ms": per_launch_s * 1e3},
-        "sweep_gups": N / per_launch_s / 1e9,
+        "sweep_gups": N * fuse / per_launch_s / 1e9,
+        "slope_roofline_frac": (N * fuse / per_launch_s) * 0.5 / (peak * 1e9),
         "gpu_launches": launches,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": e2e_steps},
@@ -302,6 +314,9 @@ def main():
     ap.add_argument("--impl", default="okz", choices=["okz", "reference"])
     ap.add_argument("--L", type=int, default=L_DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel", default="auto", choices=sorted(KERNELS))
+    ap.add_argument("--wpt", type=int, default=0, help="words per thread (0 = library choice)")
+    ap.add_argument("--fuse", type=int, default=0, help="sweeps per launch (0 = library choice)")
     args = ap.parse_args()
     world, rank, local = _dist_init(args)
     if args.impl == "reference":

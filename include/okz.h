@@ -70,13 +70,23 @@ typedef struct okz_i128 {
     int64_t hi;
 } okz_i128;
 
-/* Which sweep kernel a simulation uses. AUTO picks STREAM when L is a
- * multiple of 4096 and at most 131072, else PLAIN. Both give bit-identical
- * results. */
+/* Which sweep kernel (and device representation) a simulation uses. All
+ * give bit-identical results; the state format of okz_state/okz_restore is
+ * always the two slope planes.
+ *  - PLAIN, STREAM keep the two slope planes of Sec. II on the device.
+ *  - PARITY_PLAIN, PARITY_STREAM keep one height-parity plane: since
+ *    h(x,y) == x + y (mod 2), the bit b = floor(h/2) mod 2 fixes h mod 4
+ *    and with it every slope (sigma_x(x,y) = +1 iff b(x+1,y) ^ b(x,y) ^
+ *    ((x+y) mod 2) == 0, likewise sigma_y), and a move toggles only the
+ *    site's own bit: one bit read and one written per site and sweep.
+ * AUTO picks PARITY_STREAM when L is a multiple of 4096 and at most
+ * 131072, else PARITY_PLAIN. */
 enum {
     OKZ_KERNEL_AUTO = 0,
-    OKZ_KERNEL_PLAIN = 1,  /* one in-place launch per half-sweep                 */
-    OKZ_KERNEL_STREAM = 2  /* one launch per sweep, TMA-staged rows, ping-pong    */
+    OKZ_KERNEL_PLAIN = 1,          /* slope planes, one in-place launch per half-sweep */
+    OKZ_KERNEL_STREAM = 2,         /* slope planes, TMA-staged rows, ping-pong         */
+    OKZ_KERNEL_PARITY_PLAIN = 3,   /* parity plane, one in-place launch per half-sweep */
+    OKZ_KERNEL_PARITY_STREAM = 4   /* parity plane, TMA-staged rows, ping-pong         */
 };
 
 typedef struct okz_params {
@@ -96,9 +106,11 @@ typedef struct okz_info {
     uint64_t t;           /* completed sweeps                                  */
     int64_t H0;           /* h(0,0)                                            */
     int32_t k;            /* acceptance precision in bits                      */
-    int32_t kernel;       /* OKZ_KERNEL_PLAIN or OKZ_KERNEL_STREAM             */
+    int32_t kernel;       /* the OKZ_KERNEL_* in use (never AUTO)              */
     uint64_t P, Q;        /* thresholds: accept iff U < P (min) / U < Q (max)  */
     size_t device_bytes;  /* device memory held by the simulation              */
+    int32_t words_per_thread;  /* stream kernels: words per thread (else 0)    */
+    int32_t sweeps_per_pass;   /* sweeps per launch                             */
 } okz_info;
 
 typedef struct okz_sim okz_sim;

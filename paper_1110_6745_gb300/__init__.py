@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libokz.so")
 OKZ_OK, OKZ_EINVAL, OKZ_ENOMEM, OKZ_ECUDA, OKZ_ETIMEOUT, OKZ_EBUSY, OKZ_EOVERFLOW, \
     OKZ_EUNSUPPORTED = range(8)
 OKZ_KERNEL_AUTO, OKZ_KERNEL_PLAIN, OKZ_KERNEL_STREAM = 0, 1, 2
+OKZ_KERNEL_PARITY_PLAIN, OKZ_KERNEL_PARITY_STREAM = 3, 4
 STATUS_NAMES = {0: "OKZ_OK", 1: "OKZ_EINVAL", 2: "OKZ_ENOMEM", 3: "OKZ_ECUDA",
                 4: "OKZ_ETIMEOUT", 5: "OKZ_EBUSY", 6: "OKZ_EOVERFLOW", 7: "OKZ_EUNSUPPORTED"}
 
@@ -46,7 +47,8 @@ class okz_params(ctypes.Structure):
 class okz_info(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int64), ("t", ctypes.c_uint64), ("H0", ctypes.c_int64),
                 ("k", ctypes.c_int32), ("kernel", ctypes.c_int32), ("P", ctypes.c_uint64),
-                ("Q", ctypes.c_uint64), ("device_bytes", ctypes.c_size_t)]
+                ("Q", ctypes.c_uint64), ("device_bytes", ctypes.c_size_t),
+                ("words_per_thread", ctypes.c_int32), ("sweeps_per_pass", ctypes.c_int32)]
 
 
 # C signatures: name -> (restype, argtypes)
@@ -265,6 +267,14 @@ class Simulation:
 
     def info(self):
         return okz_get_info(self.h)
+
+    @property
+    def wpt(self):
+        return self.info().words_per_thread
+
+    @property
+    def fuse(self):
+        return self.info().sweeps_per_pass
 
     def synchronize(self):
         okz_synchronize(self.h)

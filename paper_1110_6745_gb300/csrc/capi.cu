@@ -15,6 +15,7 @@ struct okz_sim {
   okz_params prm;
   okz::Accept acc;
   int kernel;
+  bool parity;  // device state is one height-parity plane (else two slope planes)
   int wpt;   // stream kernel: words per thread
   int fuse;  // stream kernel: sweeps per launch
   int device;
@@ -157,19 +158,22 @@ okz_status okz_create_ex(const okz_params *prm, void *dev_buf, size_t bytes, voi
   if (st != OKZ_OK) return st;
   int kernel = prm->kernel;
   if (kernel == OKZ_KERNEL_AUTO)
-    kernel = stream_kernel_supports(prm->L) ? OKZ_KERNEL_STREAM : OKZ_KERNEL_PLAIN;
-  if (kernel == OKZ_KERNEL_STREAM && !stream_kernel_supports(prm->L)) {
-    set_error("the streaming kernel needs L % 4096 == 0 and L <= 131072");
-    return OKZ_EUNSUPPORTED;
-  }
-  if (kernel != OKZ_KERNEL_PLAIN && kernel != OKZ_KERNEL_STREAM) {
+    kernel = stream_kernel_supports(prm->L) ? OKZ_KERNEL_PARITY_STREAM : OKZ_KERNEL_PARITY_PLAIN;
+  if (kernel < OKZ_KERNEL_PLAIN || kernel > OKZ_KERNEL_PARITY_STREAM) {
     set_error("unknown kernel selector");
     return OKZ_EINVAL;
   }
+  const bool streamed = kernel == OKZ_KERNEL_STREAM || kernel == OKZ_KERNEL_PARITY_STREAM;
+  if (streamed && !stream_kernel_supports(prm->L)) {
+    set_error("the streaming kernels need L % 4096 == 0 and L <= 131072");
+    return OKZ_EUNSUPPORTED;
+  }
   int wpt = prm->words_per_thread, fuse = prm->sweeps_per_pass;
-  if (kernel == OKZ_KERNEL_STREAM) {
+  if (streamed) {
+    // defaults measured on GB300: 8 words per thread where the row allows it;
+    // the parity plane fuses two sweeps per pass on large lattices
     if (wpt == 0) wpt = stream_wpt_valid(prm->L, 8) ? 8 : 4;
-    if (fuse == 0) fuse = 1;
+    if (fuse == 0) fuse = (kernel == OKZ_KERNEL_PARITY_STREAM && prm->L >= 65536) ? 2 : 1;
     if (!stream_wpt_valid(prm->L, wpt) || (fuse != 1 && fuse != 2)) {
       set_error("words_per_thread must be 4 or 8 (8 needs L % 8192 == 0) and "
                 "sweeps_per_pass 1 or 2");
@@ -195,6 +199,7 @@ okz_status okz_create_ex(const okz_params *prm, void *dev_buf, size_t bytes, voi
   sim->acc.Q = Q;
   sim->acc.k = k;
   sim->kernel = kernel;
+  sim->parity = kernel == OKZ_KERNEL_PARITY_PLAIN || kernel == OKZ_KERNEL_PARITY_STREAM;
   sim->wpt = wpt;
   sim->fuse = fuse;
   sim->lay = lay;
@@ -237,7 +242,12 @@ okz_status okz_create_ex(const okz_params *prm, void *dev_buf, size_t bytes, voi
   sim->ctrl = (Ctrl *)(sim->base + lay.off_ctrl);
 
   e = cudaMemsetAsync(sim->ctrl, 0, sizeof(Ctrl), sim->stream);
-  if (e == cudaSuccess) e = launch_init_flat(sim->planes[0], prm->L, sim->stream);
+  if (e == cudaSuccess) {
+    if (sim->parity)  // striped start: h = (x+y) mod 2, so b = 0 everywhere
+      e = cudaMemsetAsync(sim->planes[0], 0, lay.planes_bytes / 2, sim->stream);
+    else
+      e = launch_init_flat(sim->planes[0], prm->L, sim->stream);
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(sim->stream);
   if (e != cudaSuccess) {
     okz_status r = cuda_fail(e, "initialisation");
@@ -275,12 +285,23 @@ okz_status okz_sweep(okz_sim *sim, int64_t n) {
     const uint32_t t = (uint32_t)sim->t;
     cudaError_t e;
     int64_t step = 1;
-    if (sim->kernel == OKZ_KERNEL_STREAM) {
+    if (sim->kernel == OKZ_KERNEL_STREAM || sim->kernel == OKZ_KERNEL_PARITY_STREAM) {
       step = (sim->fuse == 2 && n - done >= 2) ? 2 : 1;
-      e = launch_sweep_stream(sim->planes[sim->cur], sim->planes[1 - sim->cur], L, t,
-                              sim->prm.seed, sim->acc, sim->wpt, (int)step, sim->ctrl,
-                              sim->stream);
+      if (sim->parity)
+        e = launch_parity_stream(sim->planes[sim->cur], sim->planes[1 - sim->cur], L, t,
+                                 sim->prm.seed, sim->acc, sim->wpt, (int)step, sim->ctrl,
+                                 sim->stream);
+      else
+        e = launch_sweep_stream(sim->planes[sim->cur], sim->planes[1 - sim->cur], L, t,
+                                sim->prm.seed, sim->acc, sim->wpt, (int)step, sim->ctrl,
+                                sim->stream);
       if (e == cudaSuccess) sim->cur = 1 - sim->cur;
+    } else if (sim->parity) {
+      e = launch_parity_halfsweep(sim->planes[sim->cur], L, 0, t, sim->prm.seed, sim->acc,
+                                  sim->ctrl, sim->stream);
+      if (e == cudaSuccess)
+        e = launch_parity_halfsweep(sim->planes[sim->cur], L, 1, t, sim->prm.seed, sim->acc,
+                                    sim->ctrl, sim->stream);
     } else {
       e = launch_halfsweep_plain(sim->planes[sim->cur], L, 0, t, sim->prm.seed, sim->acc,
                                  sim->ctrl, sim->stream);
@@ -320,8 +341,8 @@ void *okz_stream(okz_sim *sim) { return sim ? (void *)sim->stream : nullptr; }
 
 // Runs the power-sum kernels and reads back H0 and S_1..S_nmom (about H0).
 static okz_status power_sums(okz_sim *sim, int nmom, long long *H0, __int128 S[4]) {
-  cudaError_t e = launch_power_sums(sim->planes[sim->cur], sim->prm.L, nmom, sim->hcol,
-                                    sim->partials, sim->ctrl, sim->stream);
+  cudaError_t e = launch_power_sums(sim->planes[sim->cur], sim->prm.L, sim->parity, nmom,
+                                    sim->hcol, sim->partials, sim->ctrl, sim->stream);
   if (e != cudaSuccess) return cuda_fail(e, "power-sum launch");
   okz_status st = sync_and_check(sim);
   if (st != OKZ_OK) return st;
@@ -409,8 +430,8 @@ okz_status okz_heights(okz_sim *sim, int64_t y0, int64_t ny, int32_t *out,
   e = cudaMemcpyAsync(&sim->ctrl->err, &zero, sizeof(zero), cudaMemcpyHostToDevice,
                       sim->stream);
   if (e == cudaSuccess)
-    e = launch_heights(sim->planes[sim->cur], L, y0, ny, sim->hcol, dst, sim->ctrl,
-                       sim->stream);
+    e = launch_heights(sim->planes[sim->cur], L, sim->parity, y0, ny, sim->hcol, dst,
+                       sim->ctrl, sim->stream);
   if (e == cudaSuccess && !out_is_device)
     e = cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, sim->stream);
   if (!out_is_device) cudaFreeAsync(dst, sim->stream);
@@ -434,10 +455,23 @@ okz_status okz_state(okz_sim *sim, uint32_t *planes_out, int out_is_device, int6
     return OKZ_EINVAL;
   }
   cudaError_t e = cudaSuccess;
-  if (planes_out)
-    e = cudaMemcpyAsync(planes_out, sim->planes[sim->cur], sim->lay.planes_bytes,
-                        out_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                        sim->stream);
+  if (planes_out) {
+    const uint32_t *slopes = sim->planes[sim->cur];
+    if (sim->parity) {  // convert into the idle ping-pong buffer, then copy out
+      if (out_is_device) {
+        e = launch_to_slopes(sim->planes[sim->cur], sim->prm.L, planes_out, sim->stream);
+        slopes = nullptr;
+      } else {
+        e = launch_to_slopes(sim->planes[sim->cur], sim->prm.L, sim->planes[1 - sim->cur],
+                             sim->stream);
+        slopes = sim->planes[1 - sim->cur];
+      }
+    }
+    if (e == cudaSuccess && slopes)
+      e = cudaMemcpyAsync(planes_out, slopes, sim->lay.planes_bytes,
+                          out_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                          sim->stream);
+  }
   long long h0 = 0;
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(&h0, &sim->ctrl->H0, sizeof(h0), cudaMemcpyDeviceToHost, sim->stream);
@@ -455,11 +489,20 @@ okz_status okz_restore(okz_sim *sim, const uint32_t *planes, int in_is_device, i
     set_error("bad restore request");
     return OKZ_EINVAL;
   }
+  if (H0 & 1) {
+    set_error("H0 = h(0,0) must be even (h(x,y) == x + y mod 2)");
+    return OKZ_EINVAL;
+  }
   long long h0 = H0;
-  cudaError_t e = cudaMemcpyAsync(sim->planes[sim->cur], planes, sim->lay.planes_bytes,
+  // parity plane: stage the slopes in the idle ping-pong buffer, then convert
+  uint32_t *landing = sim->parity ? sim->planes[1 - sim->cur] : sim->planes[sim->cur];
+  cudaError_t e = cudaMemcpyAsync(landing, planes, sim->lay.planes_bytes,
                                   in_is_device ? cudaMemcpyDeviceToDevice
                                                : cudaMemcpyHostToDevice,
                                   sim->stream);
+  if (e == cudaSuccess && sim->parity)
+    e = launch_from_slopes(landing, sim->prm.L, h0, sim->hcol, sim->planes[sim->cur],
+                           sim->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(&sim->ctrl->H0, &h0, sizeof(h0), cudaMemcpyHostToDevice, sim->stream);
   if (e != cudaSuccess) return cuda_fail(e, "restore copy");
@@ -485,6 +528,8 @@ okz_status okz_get_info(okz_sim *sim, okz_info *info) {
   info->P = sim->acc.P;
   info->Q = sim->acc.Q;
   info->device_bytes = sim->lay.total;
+  info->words_per_thread = sim->wpt;
+  info->sweeps_per_pass = sim->fuse;
   return OKZ_OK;
 }
 

@@ -4,7 +4,8 @@
 // Heights are anchored at H0 = h(0,0). By zero curl every path gives the
 // same height; the kernels here go down column 0 first and then along each
 // row:  h(x,y) - H0 = sum_{y'<y} sigma_y(0,y') + sum_{x'<x} sigma_x(x',y).
-// Only the X plane and column 0 of the Y plane are read (0.125 B/site).
+// Only the X plane and column 0 of the Y plane are read (0.125 B/site); on
+// the height-parity plane (parity.cu) the slopes are formed on the fly.
 //
 // Power sums S_n = sum (h - H0)^n are exact: 64-bit per word and per thread,
 // 128-bit per thread total, then per block, then a single-block final sum.
@@ -38,8 +39,29 @@ __device__ __forceinline__ long long warp_exclusive_scan64(long long v, int lane
 
 // hcol[y] = h(0,y) - H0 = sum_{y'<y} sigma_y(0,y'): one block, each thread a
 // contiguous run of rows, block-wide exclusive scan of the run totals.
+// sigma_y(0,y) as a bit: read from the Y plane, or (parity plane B) from
+// b(0,y) ^ b(0,y+1) ^ p(0,y) == 0.
+template <bool PAR>
+__device__ __forceinline__ uint32_t col0_up(const uint32_t *__restrict__ P, int64_t L,
+                                            int64_t W, int64_t y) {
+  if (!PAR) return P[L * W + y * W] & 1u;
+  const int64_t yu = (y == L - 1) ? 0 : y + 1;
+  return ~(P[y * W] ^ P[yu * W] ^ (uint32_t)(y & 1)) & 1u;
+}
+
+// X-plane word w of row y: stored, or (parity plane) ~(b ^ b(x+1) ^ p).
+template <bool PAR>
+__device__ __forceinline__ uint32_t x_word(const uint32_t *__restrict__ row, int64_t W,
+                                           int64_t w, int64_t y) {
+  if (!PAR) return row[w];
+  const uint32_t c = row[w], n = row[w == W - 1 ? 0 : w + 1];
+  const uint32_t P = (y & 1) ? 0x55555555u : 0xAAAAAAAAu;  // sites with x + y odd
+  return ~(c ^ __funnelshift_r(c, n, 1) ^ P);
+}
+
+template <bool PAR>
 __global__ void __launch_bounds__(1024)
-colscan_kernel(const uint32_t *__restrict__ Yp, int64_t L, int64_t *__restrict__ hcol) {
+colscan_kernel(const uint32_t *__restrict__ planes, int64_t L, int64_t *__restrict__ hcol) {
   __shared__ long long warp_tot[32];
   const int64_t W = L >> 5;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -47,7 +69,7 @@ colscan_kernel(const uint32_t *__restrict__ Yp, int64_t L, int64_t *__restrict__
   const int64_t y0 = tid * R < L ? tid * R : L;
   const int64_t y1 = y0 + R < L ? y0 + R : L;
   long long run = 0;
-  for (int64_t y = y0; y < y1; ++y) run += 2 * (long long)(Yp[y * W] & 1u) - 1;
+  for (int64_t y = y0; y < y1; ++y) run += 2 * (long long)col0_up<PAR>(planes, L, W, y) - 1;
   const long long pre = warp_exclusive_scan64(run, lane);
   if (lane == 31) warp_tot[warp] = pre + run;
   __syncthreads();
@@ -61,7 +83,7 @@ colscan_kernel(const uint32_t *__restrict__ Yp, int64_t L, int64_t *__restrict__
   long long h = warp_tot[warp] + pre;
   for (int64_t y = y0; y < y1; ++y) {
     hcol[y] = h;
-    h += 2 * (long long)(Yp[y * W] & 1u) - 1;
+    h += 2 * (long long)col0_up<PAR>(planes, L, W, y) - 1;
   }
 }
 
@@ -82,7 +104,7 @@ __device__ __forceinline__ uint32_t byte_entry(uint32_t v) {
 // Row sums. Each warp owns rows y = warp id, warp id + #warps, ...; lane l
 // owns the contiguous words [l*wpl, (l+1)*wpl) of the row. NMOM = 2 gives
 // S1, S2 with the byte table; NMOM = 4 gives S1..S4 with a bit loop.
-template <int NMOM>
+template <int NMOM, bool PAR>
 __global__ void __launch_bounds__(256)
 rowsum_kernel(const uint32_t *__restrict__ Xp, int64_t L,
               const int64_t *__restrict__ hcol, unsigned long long *__restrict__ partials) {
@@ -106,12 +128,12 @@ rowsum_kernel(const uint32_t *__restrict__ Xp, int64_t L,
   for (int64_t y = gwarp; y < L; y += nwarps) {
     const uint32_t *row = Xp + y * W;
     int c = 0;
-    for (int64_t w = w0; w < w1; ++w) c += __popc(row[w]);
+    for (int64_t w = w0; w < w1; ++w) c += __popc(x_word<PAR>(row, W, w, y));
     const int d = 2 * c - 32 * (int)(w1 - w0);  // height change over my words
     long long a = hcol[y] + warp_exclusive_scan(d, lane);
     long long s1 = 0, s2 = 0;
     for (int64_t w = w0; w < w1; ++w) {
-      const uint32_t v = row[w];
+      const uint32_t v = x_word<PAR>(row, W, w, y);
       if (NMOM == 2) {
         long long es = 0, eq = 0;
         int o = 0;
@@ -185,20 +207,29 @@ static int reduce_blocks(int64_t L) {
   return (int)b;
 }
 
-cudaError_t launch_power_sums(const uint32_t *planes, int64_t L, int nmom, int64_t *hcol,
-                              unsigned long long *partials, Ctrl *ctrl, cudaStream_t st) {
-  const int64_t words = L * (L >> 5);
-  colscan_kernel<<<1, 1024, 0, st>>>(planes + words, L, hcol);
+cudaError_t launch_power_sums(const uint32_t *planes, int64_t L, bool parity, int nmom,
+                              int64_t *hcol, unsigned long long *partials, Ctrl *ctrl,
+                              cudaStream_t st) {
   const int nb = reduce_blocks(L);
-  if (nmom == 2)
-    rowsum_kernel<2><<<nb, 256, 0, st>>>(planes, L, hcol, partials);
-  else
-    rowsum_kernel<4><<<nb, 256, 0, st>>>(planes, L, hcol, partials);
+  if (parity) {
+    colscan_kernel<true><<<1, 1024, 0, st>>>(planes, L, hcol);
+    if (nmom == 2)
+      rowsum_kernel<2, true><<<nb, 256, 0, st>>>(planes, L, hcol, partials);
+    else
+      rowsum_kernel<4, true><<<nb, 256, 0, st>>>(planes, L, hcol, partials);
+  } else {
+    colscan_kernel<false><<<1, 1024, 0, st>>>(planes, L, hcol);
+    if (nmom == 2)
+      rowsum_kernel<2, false><<<nb, 256, 0, st>>>(planes, L, hcol, partials);
+    else
+      rowsum_kernel<4, false><<<nb, 256, 0, st>>>(planes, L, hcol, partials);
+  }
   partials_sum_kernel<<<1, 256, 0, st>>>(partials, nb, nmom, ctrl);
   return cudaGetLastError();
 }
 
 // h(x, y0 + r) for r < ny as int32, row-major; flags heights outside int32.
+template <bool PAR>
 __global__ void __launch_bounds__(256)
 heights_kernel(const uint32_t *__restrict__ Xp, int64_t L, int64_t y0, int64_t ny,
                const int64_t *__restrict__ hcol, int32_t *__restrict__ out,
@@ -216,12 +247,12 @@ heights_kernel(const uint32_t *__restrict__ Xp, int64_t L, int64_t y0, int64_t n
     const int64_t y = y0 + r;
     const uint32_t *row = Xp + y * W;
     int c = 0;
-    for (int64_t w = w0; w < w1; ++w) c += __popc(row[w]);
+    for (int64_t w = w0; w < w1; ++w) c += __popc(x_word<PAR>(row, W, w, y));
     const int d = 2 * c - 32 * (int)(w1 - w0);
     long long h = H0 + hcol[y] + warp_exclusive_scan(d, lane);
     int32_t *o = out + r * L;
     for (int64_t w = w0; w < w1; ++w) {
-      const uint32_t v = row[w];
+      const uint32_t v = x_word<PAR>(row, W, w, y);
       for (int b = 0; b < 32; ++b) {
         bad |= (h < INT32_MIN) || (h > INT32_MAX);
         o[32 * w + b] = (int32_t)h;
@@ -232,14 +263,19 @@ heights_kernel(const uint32_t *__restrict__ Xp, int64_t L, int64_t y0, int64_t n
   if (bad) atomicOr(&ctrl->err, kErrHeightRange);
 }
 
-cudaError_t launch_heights(const uint32_t *planes, int64_t L, int64_t y0, int64_t ny,
-                           int64_t *hcol, int32_t *out, Ctrl *ctrl, cudaStream_t st) {
-  const int64_t words = L * (L >> 5);
-  colscan_kernel<<<1, 1024, 0, st>>>(planes + words, L, hcol);
+cudaError_t launch_heights(const uint32_t *planes, int64_t L, bool parity, int64_t y0,
+                           int64_t ny, int64_t *hcol, int32_t *out, Ctrl *ctrl,
+                           cudaStream_t st) {
   int64_t nb = (ny + 7) / 8;
   if (nb > 152 * 16) nb = 152 * 16;
   if (nb < 1) nb = 1;
-  heights_kernel<<<(unsigned)nb, 256, 0, st>>>(planes, L, y0, ny, hcol, out, ctrl);
+  if (parity) {
+    colscan_kernel<true><<<1, 1024, 0, st>>>(planes, L, hcol);
+    heights_kernel<true><<<(unsigned)nb, 256, 0, st>>>(planes, L, y0, ny, hcol, out, ctrl);
+  } else {
+    colscan_kernel<false><<<1, 1024, 0, st>>>(planes, L, hcol);
+    heights_kernel<false><<<(unsigned)nb, 256, 0, st>>>(planes, L, y0, ny, hcol, out, ctrl);
+  }
   return cudaGetLastError();
 }
 

@@ -1,0 +1,591 @@
+// parity.cu -- the octahedron model on a single height-parity bit-plane.
+//
+// Heights of the octahedron model satisfy h(x,y) == x + y (mod 2) (Kelling &
+// Odor, arXiv:1110.6745, Sec. I: neighbours differ by exactly 1). Writing
+// h = p + 2k with p = (x+y) mod 2, one bit per site, b = k mod 2 (h mod 4
+// given p), fixes every slope:
+//     sigma_x(x,y) = +1  <=>  b(x+1,y) ^ b(x,y) ^ p(x,y) == 0,
+//     sigma_y(x,y) = +1  <=>  b(x,y+1) ^ b(x,y) ^ p(x,y) == 0,
+// so the two slope planes of Sec. II carry one redundant bit per site. In
+// this encoding the rule of Eq. (2) reads: a site of half-sweep s (p = s) is
+// a local minimum iff all four neighbours have b == b(x,y) ^ s, a local
+// maximum iff all four have b == !(b(x,y) ^ s), and a move (h += 2 or
+// h -= 2) toggles only the site's own bit. A sweep therefore reads one bit
+// and writes one bit per site (0.25 B/site) and no bond is shared.
+//
+// Layout: L rows of L/32 little-endian uint32 words; bit b of word w of row y
+// is site x = 32w + b. The C-ABI state format stays the slope planes;
+// to_slopes / from_slopes convert at the boundary.
+#include <cuda_runtime.h>
+
+#include "okz_internal.h"
+#include "okz_tma.cuh"
+
+namespace okz {
+
+namespace {
+
+// Sites of row y with p(x,y) = (x+y) mod 2 == 1.
+__device__ __forceinline__ uint32_t odd_mask(int64_t y) {
+  return (y & 1) ? 0x55555555u : 0xAAAAAAAAu;
+}
+
+// Minima and maxima of 32 sites: c = own bits ^ S (S = all ones for s = 1),
+// l, r, d, u = the left, right, lower and upper neighbours' bits.
+__device__ __forceinline__ void parity_extrema(uint32_t c, uint32_t l, uint32_t r, uint32_t d,
+                                               uint32_t u, uint32_t a, uint32_t &mn,
+                                               uint32_t &mx) {
+  const uint32_t dl = l ^ c, dr = r ^ c, dd = d ^ c, du = u ^ c;
+  mn = a & ~(dl | dr | dd | du);
+  mx = a & dl & dr & dd & du;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// In-place half-sweep, one thread per 128-site group. A flip changes only the
+// site's own bit, and every bit a thread reads from a neighbouring word sits
+// on a site of the other sublattice, which nobody writes in this half-sweep;
+// whole-word stores therefore never change a bit another thread uses.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+parity_halfsweep_kernel(uint32_t *__restrict__ B, int64_t L, int s, uint32_t t,
+                        uint64_t seed, Accept acc, Ctrl *__restrict__ ctrl) {
+  const int64_t W = L >> 5;
+  const int64_t groups = L * W >> 2;
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= groups) return;
+  uint32_t mn[4], mx[4], ctr[4];
+  int64_t idx[4];
+  const uint32_t S = s ? ~0u : 0u;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int64_t gw = 4 * g + j;
+    const int64_t y = gw / W, w = gw - y * W;
+    const int64_t wl = (w == 0) ? W - 1 : w - 1, wr = (w == W - 1) ? 0 : w + 1;
+    const int64_t yd = (y == 0) ? L - 1 : y - 1, yu = (y == L - 1) ? 0 : y + 1;
+    idx[j] = gw;
+    ctr[j] = B[gw];
+    const uint32_t l = __funnelshift_l(B[y * W + wl], ctr[j], 1);  // b(x-1)
+    const uint32_t r = __funnelshift_r(ctr[j], B[y * W + wr], 1);  // b(x+1)
+    parity_extrema(ctr[j] ^ S, l, r, B[yd * W + w], B[yu * W + w], active_mask(y, s), mn[j],
+                   mx[j]);
+  }
+  const uint64_t full = 1ull << acc.k;
+  uint32_t ltp[4], eqp[4], ltq[4], eqq[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    ltp[j] = (acc.P >= full) ? mn[j] : 0u;
+    eqp[j] = (acc.P >= full || acc.P == 0) ? 0u : mn[j];
+    ltq[j] = (acc.Q >= full) ? mx[j] : 0u;
+    eqq[j] = (acc.Q >= full || acc.Q == 0) ? 0u : mx[j];
+  }
+  for (int m = 0; m < acc.k; ++m) {
+    if (((eqp[0] | eqq[0]) | (eqp[1] | eqq[1]) | (eqp[2] | eqq[2]) | (eqp[3] | eqq[3])) == 0u)
+      break;
+    const u32x4 r = group_bits((uint64_t)g, t, (uint32_t)m, seed);
+    const uint32_t pb = (uint32_t)(acc.P >> (acc.k - 1 - m)) & 1u;
+    const uint32_t qb = (uint32_t)(acc.Q >> (acc.k - 1 - m)) & 1u;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      lt_step(r.v[j], pb, ltp[j], eqp[j]);
+      lt_step(r.v[j], qb, ltq[j], eqq[j]);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const uint32_t f = ltp[j] | ltq[j];
+    if (f == 0u) continue;
+    B[idx[j]] = ctr[j] ^ f;
+    if (idx[j] == 0 && (f & 1u)) ctrl->H0 += (mn[0] & 1u) ? 2 : -2;  // site (0,0)
+  }
+}
+
+cudaError_t launch_parity_halfsweep(uint32_t *B, int64_t L, int s, uint32_t t, uint64_t seed,
+                                    const Accept &acc, Ctrl *ctrl, cudaStream_t st) {
+  const int64_t groups = L * (L >> 5) / 4;
+  parity_halfsweep_kernel<<<(unsigned)((groups + 255) / 256), 256, 0, st>>>(B, L, s, t, seed,
+                                                                              acc, ctrl);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Boundary conversions.
+// ---------------------------------------------------------------------------
+__global__ void to_slopes_kernel(const uint32_t *__restrict__ B, int64_t L,
+                                 uint32_t *__restrict__ out) {
+  const int64_t W = L >> 5, words = L * W;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < words;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t y = i / W, w = i - y * W;
+    const int64_t wr = (w == W - 1) ? 0 : w + 1, yu = (y == L - 1) ? 0 : y + 1;
+    const uint32_t c = B[i];
+    const uint32_t r = __funnelshift_r(c, B[y * W + wr], 1);
+    const uint32_t P = odd_mask(y);
+    out[i] = ~(c ^ r ^ P);               // sigma_x = +1 where b(x+1) ^ b ^ p == 0
+    out[words + i] = ~(c ^ B[yu * W + w] ^ P);  // sigma_y
+  }
+}
+
+cudaError_t launch_to_slopes(const uint32_t *B, int64_t L, uint32_t *out, cudaStream_t st) {
+  const int64_t words = L * (L >> 5);
+  int64_t blocks = (words + 255) / 256;
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  to_slopes_kernel<<<(unsigned)blocks, 256, 0, st>>>(B, L, out);
+  return cudaGetLastError();
+}
+
+// b(0,y): b(0,0) = (H0/2) mod 2, b(0,y+1) = b(0,y) ^ p(0,y) ^ !sigma_y-bit(0,y).
+// One block; each thread a run of rows; block-wide exclusive xor-scan.
+__global__ void __launch_bounds__(1024)
+from_slopes_col_kernel(const uint32_t *__restrict__ slopes, int64_t L, long long H0,
+                       int64_t *__restrict__ bcol) {
+  __shared__ uint32_t warp_x[32];
+  const int64_t W = L >> 5;
+  const uint32_t *Yp = slopes + L * W;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t R = (L + blockDim.x - 1) / blockDim.x;
+  const int64_t y0 = tid * R < L ? tid * R : L;
+  const int64_t y1 = y0 + R < L ? y0 + R : L;
+  uint32_t run = 0;
+  for (int64_t y = y0; y < y1; ++y) run ^= ((uint32_t)y & 1u) ^ (~Yp[y * W] & 1u);
+  uint32_t inc = run;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t n = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+    if (lane >= o) inc ^= n;
+  }
+  if (lane == 31) warp_x[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = blockDim.x >> 5;
+    uint32_t v = lane < nw ? warp_x[lane] : 0u, iv = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t n = __shfl_up_sync(0xFFFFFFFFu, iv, o);
+      if (lane >= o) iv ^= n;
+    }
+    if (lane < nw) warp_x[lane] = iv ^ v;  // exclusive
+  }
+  __syncthreads();
+  uint32_t b = (uint32_t)((H0 >> 1) & 1) ^ warp_x[warp] ^ inc ^ run;
+  for (int64_t y = y0; y < y1; ++y) {
+    bcol[y] = b;
+    b ^= ((uint32_t)y & 1u) ^ (~Yp[y * W] & 1u);
+  }
+}
+
+// Rows: b(x+1,y) = b(x,y) ^ p(x,y) ^ !sigma_x-bit(x,y). A warp per row, each
+// lane a run of words; in-word exclusive prefix xor, warp xor-scan of carries.
+__global__ void __launch_bounds__(256)
+from_slopes_row_kernel(const uint32_t *__restrict__ slopes, int64_t L,
+                       const int64_t *__restrict__ bcol, uint32_t *__restrict__ B) {
+  const int lane = threadIdx.x & 31;
+  const int64_t W = L >> 5;
+  const int64_t wpl = (W + 31) >> 5;
+  const int64_t w0 = lane * wpl < W ? lane * wpl : W;
+  const int64_t w1 = w0 + wpl < W ? w0 + wpl : W;
+  const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t y = gwarp; y < L; y += nwarps) {
+    const uint32_t P = odd_mask(y);
+    uint32_t par = 0;
+    for (int64_t w = w0; w < w1; ++w) par ^= __popc(P ^ ~slopes[y * W + w]) & 1u;
+    uint32_t inc = par;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t n = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+      if (lane >= o) inc ^= n;
+    }
+    uint32_t carry = (uint32_t)bcol[y] ^ inc ^ par;  // b at my first site
+    for (int64_t w = w0; w < w1; ++w) {
+      const uint32_t d = P ^ ~slopes[y * W + w];  // bit x: b(x+1) ^ b(x)
+      uint32_t e = d;                             // inclusive prefix xor
+      e ^= e << 1;
+      e ^= e << 2;
+      e ^= e << 4;
+      e ^= e << 8;
+      e ^= e << 16;
+      B[y * W + w] = (e ^ d) ^ (carry ? ~0u : 0u);  // exclusive prefix ^ carry
+      carry ^= __popc(d) & 1u;
+    }
+  }
+}
+
+cudaError_t launch_from_slopes(const uint32_t *slopes, int64_t L, long long H0, int64_t *bcol,
+                               uint32_t *B, cudaStream_t st) {
+  from_slopes_col_kernel<<<1, 1024, 0, st>>>(slopes, L, H0, bcol);
+  int64_t nb = (L + 7) / 8;
+  if (nb > 152 * 16) nb = 152 * 16;
+  from_slopes_row_kernel<<<(unsigned)nb, 256, 0, st>>>(slopes, L, bcol, B);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Streaming kernel: F sweeps (2F half-sweep "stages") per launch; a CTA spans
+// full rows (L/(32*WPT) threads, WPT words each) and owns a band [yb, ye).
+// Stream row r (one 1-D TMA copy into a ring slot) drives a wavefront:
+//   stage 0 (half-sweep 0 of sweep t) processes row r-1 from the ring rows
+//       r-2, r-1, r;
+//   stage h > 0 processes row r-1-h from stage h-1's outputs: two carried
+//       rows (Wd = two steps ago, Wc = one step ago) and this step's output.
+// Output rows depend only on their own inputs (a move toggles only the site's
+// own bit), so nothing is masked or pulled. The x-neighbour bits of each
+// carried row are exchanged once per stream row (warp shuffles, shared memory
+// across warps, one CTA barrier that also recycles the ring slot of row r-2).
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kPModeHalf = 0, kPModeK1 = 1, kPModeGen = 2;
+
+struct PModes {
+  uint32_t p1, p2, q1, q2;  // k <= 1: all-ones masks for "bit must be 0" and "always"
+};
+
+template <int WPT, int MODE>
+__device__ __forceinline__ void pstage(const uint32_t c[WPT], uint32_t lbit, uint32_t rbit,
+                                       const uint32_t d[WPT], const uint32_t u[WPT], uint32_t S,
+                                       uint32_t a, const uint32_t r0[WPT], uint32_t g0,
+                                       uint32_t t, uint64_t seed, const Accept &acc,
+                                       const PModes &md, uint32_t f[WPT], uint32_t *mn0) {
+  uint32_t mn[WPT], mx[WPT];
+#pragma unroll
+  for (int j = 0; j < WPT; ++j) {
+    const uint32_t l = (c[j] << 1) | (j == 0 ? lbit : (c[j - 1] >> 31));
+    const uint32_t r = (c[j] >> 1) | ((j == WPT - 1 ? rbit : (c[j + 1] & 1u)) << 31);
+    parity_extrema(c[j] ^ S, l, r, d[j], u[j], a, mn[j], mx[j]);
+  }
+  *mn0 = mn[0];
+  if (MODE == kPModeHalf) {
+#pragma unroll
+    for (int j = 0; j < WPT; ++j) f[j] = mn[j] & ~r0[j];
+  } else if (MODE == kPModeK1) {
+#pragma unroll
+    for (int j = 0; j < WPT; ++j)
+      f[j] = (mn[j] & ((~r0[j] & md.p1) | md.p2)) | (mx[j] & ((~r0[j] & md.q1) | md.q2));
+  } else {
+    const uint64_t full = 1ull << acc.k;
+    uint32_t ltp[WPT], eqp[WPT], ltq[WPT], eqq[WPT];
+    uint32_t any = 0;
+#pragma unroll
+    for (int j = 0; j < WPT; ++j) {
+      ltp[j] = (acc.P >= full) ? mn[j] : 0u;
+      eqp[j] = (acc.P >= full || acc.P == 0) ? 0u : mn[j];
+      ltq[j] = (acc.Q >= full) ? mx[j] : 0u;
+      eqq[j] = (acc.Q >= full || acc.Q == 0) ? 0u : mx[j];
+      any |= eqp[j] | eqq[j];
+    }
+    for (int m = 0; m < acc.k && any != 0u; ++m) {
+      uint32_t rr[WPT];
+      if (m == 0) {
+#pragma unroll
+        for (int j = 0; j < WPT; ++j) rr[j] = r0[j];
+      } else {
+#pragma unroll
+        for (int gq = 0; gq < WPT / 4; ++gq) {
+          const u32x4 b = group_bits((uint64_t)(g0 + gq), t, (uint32_t)m, seed);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) rr[4 * gq + j] = b.v[j];
+        }
+      }
+      const uint32_t pb = (uint32_t)(acc.P >> (acc.k - 1 - m)) & 1u;
+      const uint32_t qb = (uint32_t)(acc.Q >> (acc.k - 1 - m)) & 1u;
+      any = 0;
+#pragma unroll
+      for (int j = 0; j < WPT; ++j) {
+        lt_step(rr[j], pb, ltp[j], eqp[j]);
+        lt_step(rr[j], qb, ltq[j], eqq[j]);
+        any |= eqp[j] | eqq[j];
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < WPT; ++j) f[j] = ltp[j] | ltq[j];
+  }
+}
+
+}  // namespace
+
+template <int WPT, int F, int MODE>
+__global__ void __launch_bounds__(WPT == 4 ? 1024 : 512, 1)
+parity_stream_kernel(const uint32_t *__restrict__ src, uint32_t *__restrict__ dst, int L,
+                     int stages, uint32_t t0, uint64_t seed, Accept acc, PModes md,
+                     Ctrl *__restrict__ ctrl) {
+  constexpr int NST = 2 * F;
+  constexpr int NC = NST > 1 ? NST - 1 : 1;  // stages whose output is carried
+  constexpr int NG = WPT / 4;
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int nthr = blockDim.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nwarps = nthr >> 5;
+  const uint32_t W = (uint32_t)L >> 5;
+  const uint32_t rowbytes = (uint32_t)L >> 3;
+  const uint32_t groups_per_row = (uint32_t)L >> 7;
+
+  unsigned char *ring = smem;  // stages x one row of b
+  uint64_t *full = (uint64_t *)(smem + (size_t)stages * rowbytes);
+  uint32_t *exL = (uint32_t *)(full + stages);  // [2][32]: value of lane 0
+  uint32_t *exR = exL + 2 * 32;                 // [2][32]: value of lane 31
+
+  const int yb = (int)((int64_t)blockIdx.x * L / gridDim.x);
+  const int ye = (int)((int64_t)(blockIdx.x + 1) * L / gridDim.x);
+  const int nin = ye - yb + 4 * F;  // stream rows yb-2F .. ye+2F-1
+
+  int p_row = yb - 2 * F;  // producer (thread 0): next row to load, its slot
+  if (p_row < 0) p_row += L;
+  int p_slot = 0;
+  auto issue = [&]() {
+    tma::mbar_expect_tx(&full[p_slot], rowbytes);
+    tma::load_1d(ring + (size_t)p_slot * rowbytes, src + (size_t)p_row * W, rowbytes,
+                 &full[p_slot]);
+    if (++p_row == L) p_row = 0;
+    if (++p_slot == stages) p_slot = 0;
+  };
+
+  if (tid == 0) {
+    for (int s = 0; s < stages; ++s) tma::mbar_init(&full[s], 1);
+    tma::mbar_init_fence();
+  }
+  __syncthreads();
+  if (tid == 0)
+    for (int i = 0; i < stages && i < nin; ++i) issue();
+
+  uint32_t Wd[NC][WPT], Wc[NC][WPT];  // stage h's outputs two / one steps ago
+  uint32_t WL[NC], WR[NC];            // x-neighbour bits of Wc[h]
+  uint32_t R[F][WPT];                 // level-0 words of the row stage 2j saw last step
+#pragma unroll
+  for (int h = 0; h < NC; ++h) {
+    WL[h] = 0;
+    WR[h] = 0;
+#pragma unroll
+    for (int j = 0; j < WPT; ++j) {
+      Wd[h][j] = 0;
+      Wc[h][j] = 0;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < F; ++q)
+#pragma unroll
+    for (int j = 0; j < WPT; ++j) R[q][j] = 0;
+
+  const uint32_t w0 = (uint32_t)(WPT * tid);
+  const uint32_t wprev = (w0 == 0) ? W - 1 : w0 - 1;
+  const uint32_t wnext = (w0 + WPT == W) ? 0 : w0 + WPT;
+  int slot = 0, sl1 = stages - 1, sl2 = stages - 2;  // slots of positions i, i-1, i-2
+  uint32_t phase = 0;
+  int y = yb - 2 * F;  // wrapped row of stream position i
+  if (y < 0) y += L;
+  const int r_origin = yb - 2 * F;
+
+  for (int i = 0; i < nin; ++i) {
+    const bool ok = tma::mbar_wait(&full[slot], phase);
+    uint32_t out[NST][WPT];
+    uint32_t fbit[NST], mn0[NST];
+    const bool active = i >= 2;  // rows r-2, r-1, r are in the ring
+    if (active) {
+      const unsigned char *ru = ring + (size_t)slot * rowbytes;  // row r   (above)
+      const unsigned char *rc = ring + (size_t)sl1 * rowbytes;   // row r-1
+      const unsigned char *rd = ring + (size_t)sl2 * rowbytes;   // row r-2 (below)
+      uint32_t cu[WPT], cc[WPT], cd[WPT];
+#pragma unroll
+      for (int gq = 0; gq < NG; ++gq) {
+        const uint4 a = *(const uint4 *)(ru + 4 * (w0 + 4 * gq));
+        const uint4 b = *(const uint4 *)(rc + 4 * (w0 + 4 * gq));
+        const uint4 e = *(const uint4 *)(rd + 4 * (w0 + 4 * gq));
+        cu[4 * gq] = a.x; cu[4 * gq + 1] = a.y; cu[4 * gq + 2] = a.z; cu[4 * gq + 3] = a.w;
+        cc[4 * gq] = b.x; cc[4 * gq + 1] = b.y; cc[4 * gq + 2] = b.z; cc[4 * gq + 3] = b.w;
+        cd[4 * gq] = e.x; cd[4 * gq + 1] = e.y; cd[4 * gq + 2] = e.z; cd[4 * gq + 3] = e.w;
+      }
+      const uint32_t lb = *(const uint32_t *)(rc + 4 * wprev) >> 31;
+      const uint32_t rb = *(const uint32_t *)(rc + 4 * wnext) & 1u;
+      uint32_t Rn[F][WPT];
+#pragma unroll
+      for (int h = 0; h < NST; ++h) {
+        int q = y - 1 - h;
+        if (q < 0) q += L;
+        const int s = h & 1;
+        const uint32_t t = t0 + (uint32_t)(h >> 1);
+        const uint32_t g0 = (uint32_t)q * groups_per_row + (uint32_t)(NG * tid);
+        if (s == 0) {  // fresh level-0 words of row q, sweep t
+#pragma unroll
+          for (int gq = 0; gq < NG; ++gq) {
+            const u32x4 b = group_bits((uint64_t)(g0 + gq), t, 0u, seed);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) Rn[h >> 1][4 * gq + j] = b.v[j];
+          }
+        }
+        const uint32_t *c = (h == 0) ? cc : Wc[h > 0 ? h - 1 : 0];
+        const uint32_t *d = (h == 0) ? cd : Wd[h > 0 ? h - 1 : 0];
+        const uint32_t *u = (h == 0) ? cu : out[h > 0 ? h - 1 : 0];
+        const uint32_t lbit = (h == 0) ? lb : WL[h > 0 ? h - 1 : 0];
+        const uint32_t rbit = (h == 0) ? rb : WR[h > 0 ? h - 1 : 0];
+        uint32_t f[WPT];
+        // s = 1 uses the words of the same row drawn by stage h-1 last step
+        pstage<WPT, MODE>(c, lbit, rbit, d, u, s ? ~0u : 0u, active_mask(q, s),
+                          s == 0 ? Rn[h >> 1] : R[h >> 1], g0, t, seed, acc, md, f, &mn0[h]);
+        fbit[h] = f[0] & 1u;
+#pragma unroll
+        for (int j = 0; j < WPT; ++j) out[h][j] = c[j] ^ f[j];
+        if (s == 1) {
+#pragma unroll
+          for (int j = 0; j < WPT; ++j) R[h >> 1][j] = Rn[h >> 1][j];
+        }
+      }
+      // H0 = h(0,0): site (0,0) moves in the s = 0 stages; only CTA 0 meets
+      // the unwrapped row 0 (CTA bands are at least 32 rows high)
+      if (tid == 0) {
+        const int r = r_origin + i;
+#pragma unroll
+        for (int h = 0; h < NST; h += 2)
+          if (r - 1 - h == 0 && fbit[h]) ctrl->H0 += (mn0[h] & 1u) ? 2 : -2;
+      }
+    }
+
+    // exchange: bits 2h / 2h+1 = first / last bit of stage h's output row
+    uint32_t v = 0;
+    if (active) {
+#pragma unroll
+      for (int h = 0; h < NC; ++h)
+        v |= ((out[h][0] & 1u) << (2 * h)) | ((out[h][WPT - 1] >> 31) << (2 * h + 1));
+    }
+    uint32_t vr = __shfl_down_sync(0xFFFFFFFFu, v, 1);
+    uint32_t vl = __shfl_up_sync(0xFFFFFFFFu, v, 1);
+    const int par = i & 1;
+    if (lane == 0) exL[par * 32 + warp] = v;
+    if (lane == 31) exR[par * 32 + warp] = v;
+    const int bad = __syncthreads_or(!ok);
+    if (bad) {
+      if (tid == 0) {
+        atomicOr(&ctrl->err, kErrWaitTimeout);
+        // give copies already issued a bounded chance to land before exiting
+        int issued = (i >= 2 ? i - 2 : 0) + stages;
+        if (issued > nin) issued = nin;
+        for (int k = i + 1; k < issued; ++k)
+          (void)tma::mbar_wait(&full[k % stages], (uint32_t)((k / stages) & 1));
+      }
+      return;
+    }
+    if (lane == 31) vr = exL[par * 32 + (warp + 1 == nwarps ? 0 : warp + 1)];
+    if (lane == 0) vl = exR[par * 32 + (warp == 0 ? nwarps - 1 : warp - 1)];
+
+    // the slot of stream row r-2 is free: refill it with row r-2+stages
+    if (tid == 0 && active && i - 2 + stages < nin) {
+      tma::fence_proxy_async();
+      issue();
+    }
+
+    if (active) {
+      const int rr = r_origin + i - NST;  // the last stage finished row r-NST
+      if (rr >= yb && rr < ye) {
+        int q = y - NST;
+        if (q < 0) q += L;
+        uint32_t *o = dst + (size_t)q * W + w0;
+#pragma unroll
+        for (int gq = 0; gq < NG; ++gq)
+          *(uint4 *)(o + 4 * gq) = make_uint4(out[NST - 1][4 * gq], out[NST - 1][4 * gq + 1],
+                                              out[NST - 1][4 * gq + 2],
+                                              out[NST - 1][4 * gq + 3]);
+      }
+#pragma unroll
+      for (int h = 0; h < NC; ++h) {
+#pragma unroll
+        for (int j = 0; j < WPT; ++j) {
+          Wd[h][j] = Wc[h][j];
+          Wc[h][j] = out[h][j];
+        }
+        WL[h] = (vl >> (2 * h + 1)) & 1u;  // left neighbour's last bit
+        WR[h] = (vr >> (2 * h)) & 1u;      // right neighbour's first bit
+      }
+    }
+
+    if (++slot == stages) {
+      slot = 0;
+      phase ^= 1u;
+    }
+    if (++sl1 == stages) sl1 = 0;
+    if (++sl2 == stages) sl2 = 0;
+    if (++y == L) y = 0;
+  }
+}
+
+namespace {
+
+struct PPlan {
+  int threads, stages, grid;
+  size_t smem;
+};
+
+PPlan pplan_for(int L, int wpt, const void *fn) {
+  PPlan p;
+  p.threads = L / (32 * wpt);
+  const size_t slot = (size_t)(L / 8);
+  int stages = (int)((200 * 1024) / slot);
+  if (stages > 12) stages = 12;
+  if (stages < 4) stages = 4;
+  p.stages = stages;
+  p.smem = (size_t)stages * slot + (size_t)stages * 8 + 2 * 2 * 32 * 4;
+  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+  int dev = 0, sms = 0, per_sm = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, p.threads, p.smem);
+  if (per_sm < 1) per_sm = 1;
+  int grid = sms * per_sm;
+  if (grid > L / 32) grid = L / 32;  // at least 32 rows per band
+  if (grid < 1) grid = 1;
+  p.grid = grid;
+  return p;
+}
+
+template <int WPT, int F, int MODE>
+cudaError_t plaunch(const uint32_t *src, uint32_t *dst, int L, uint32_t t, uint64_t seed,
+                    const Accept &acc, const PModes &md, Ctrl *ctrl, cudaStream_t st) {
+  static thread_local int cached_L = 0;
+  static thread_local PPlan plan;
+  const void *fn = (const void *)parity_stream_kernel<WPT, F, MODE>;
+  if (cached_L != L) {
+    plan = pplan_for(L, WPT, fn);
+    cached_L = L;
+  }
+  parity_stream_kernel<WPT, F, MODE><<<plan.grid, plan.threads, plan.smem, st>>>(
+      src, dst, L, plan.stages, t, seed, acc, md, ctrl);
+  return cudaGetLastError();
+}
+
+template <int MODE>
+cudaError_t plaunch_mode(const uint32_t *src, uint32_t *dst, int L, uint32_t t, uint64_t seed,
+                         const Accept &acc, const PModes &md, int wpt, int fuse, Ctrl *ctrl,
+                         cudaStream_t st) {
+  if (wpt == 8) {
+    if (fuse == 2) return plaunch<8, 2, MODE>(src, dst, L, t, seed, acc, md, ctrl, st);
+    return plaunch<8, 1, MODE>(src, dst, L, t, seed, acc, md, ctrl, st);
+  }
+  if (fuse == 2) return plaunch<4, 2, MODE>(src, dst, L, t, seed, acc, md, ctrl, st);
+  return plaunch<4, 1, MODE>(src, dst, L, t, seed, acc, md, ctrl, st);
+}
+
+}  // namespace
+
+cudaError_t launch_parity_stream(const uint32_t *src, uint32_t *dst, int64_t L, uint32_t t,
+                                 uint64_t seed, const Accept &acc, int wpt, int fuse,
+                                 Ctrl *ctrl, cudaStream_t st) {
+  PModes md{0, 0, 0, 0};
+  int mode = kPModeGen;
+  if (acc.k <= 1) {
+    const uint64_t full = 1ull << acc.k;
+    auto sel = [&](uint64_t T) { return T == 0 ? 0 : (T >= full ? 2 : 1); };
+    const int pm = sel(acc.P), qm = sel(acc.Q);
+    md.p1 = pm == 1 ? ~0u : 0u;
+    md.p2 = pm == 2 ? ~0u : 0u;
+    md.q1 = qm == 1 ? ~0u : 0u;
+    md.q2 = qm == 2 ? ~0u : 0u;
+    mode = (pm == 1 && qm == 0) ? kPModeHalf : kPModeK1;
+  }
+  const int Li = (int)L;
+  if (mode == kPModeHalf)
+    return plaunch_mode<kPModeHalf>(src, dst, Li, t, seed, acc, md, wpt, fuse, ctrl, st);
+  if (mode == kPModeK1)
+    return plaunch_mode<kPModeK1>(src, dst, Li, t, seed, acc, md, wpt, fuse, ctrl, st);
+  return plaunch_mode<kPModeGen>(src, dst, Li, t, seed, acc, md, wpt, fuse, ctrl, st);
+}
+
+}  // namespace okz

@@ -44,12 +44,17 @@ MODES = [  # p, q, s_sel: k and kernel path
 ]
 
 
+PLAIN_KINDS = [1, 3]   # OKZ_KERNEL_PLAIN (slope planes), OKZ_KERNEL_PARITY_PLAIN
+STREAM_KINDS = [2, 4]  # OKZ_KERNEL_STREAM, OKZ_KERNEL_PARITY_STREAM
+
+
+@pytest.mark.parametrize("kernel", PLAIN_KINDS)
 @pytest.mark.parametrize("L", [32, 64, 96, 128, 256, 480])
 @pytest.mark.parametrize("p,q,s_sel", MODES)
-def test_plain_kernel_matches_oracle(okz, orc, L, p, q, s_sel):
+def test_plain_kernel_matches_oracle(okz, orc, L, p, q, s_sel, kernel):
     seed = 1000 + L
     ref = orc.Sim(L, p, q, seed, s_sel=s_sel)
-    with okz.Simulation(L, p, q, seed=seed, s_sel=s_sel, kernel=okz.OKZ_KERNEL_PLAIN) as sim:
+    with okz.Simulation(L, p, q, seed=seed, s_sel=s_sel, kernel=kernel) as sim:
         for n in (1, 2, 7):
             ref.sweep(n)
             sim.sweep(n)
@@ -58,12 +63,13 @@ def test_plain_kernel_matches_oracle(okz, orc, L, p, q, s_sel):
             assert (S1, S2) == ref.sums() and W2 == ref.width2()
 
 
+@pytest.mark.parametrize("kernel", STREAM_KINDS)
 @pytest.mark.parametrize("L", [4096, 12288])
 @pytest.mark.parametrize("p,q,s_sel", MODES)
-def test_stream_kernel_matches_oracle(okz, orc, L, p, q, s_sel):
+def test_stream_kernel_matches_oracle(okz, orc, L, p, q, s_sel, kernel):
     seed = 77 + L
     ref = orc.Sim(L, p, q, seed, s_sel=s_sel)
-    with okz.Simulation(L, p, q, seed=seed, s_sel=s_sel, kernel=okz.OKZ_KERNEL_STREAM) as sim:
+    with okz.Simulation(L, p, q, seed=seed, s_sel=s_sel, kernel=kernel) as sim:
         for n in (1, 3):
             ref.sweep(n)
             sim.sweep(n)
@@ -72,15 +78,16 @@ def test_stream_kernel_matches_oracle(okz, orc, L, p, q, s_sel):
         assert (S1, S2) == ref.sums() and W2 == ref.width2()
 
 
+@pytest.mark.parametrize("kernel", STREAM_KINDS)
 @pytest.mark.parametrize("wpt,fuse", [(4, 1), (8, 1), (4, 2), (8, 2)])
 @pytest.mark.parametrize("p,q,s_sel", [(1.0, 0.0, 0.5), (0.75, 0.25, 0.5), (1.0, 1.0, 0.5),
                                        (0.95, 0.05, 0.5)])
-def test_stream_variants_match_oracle(okz, orc, wpt, fuse, p, q, s_sel):
+def test_stream_variants_match_oracle(okz, orc, wpt, fuse, p, q, s_sel, kernel):
     """Every tiling (words per thread) and temporal-blocking depth (sweeps per
     launch) gives the oracle's lattice, including odd sweep counts."""
     L, seed = 8192, 31
     ref = orc.Sim(L, p, q, seed, s_sel=s_sel)
-    with okz.Simulation(L, p, q, seed=seed, s_sel=s_sel, kernel=okz.OKZ_KERNEL_STREAM,
+    with okz.Simulation(L, p, q, seed=seed, s_sel=s_sel, kernel=kernel,
                         words_per_thread=wpt, sweeps_per_pass=fuse) as sim:
         for n in (1, 2, 3):
             ref.sweep(n)
@@ -90,11 +97,12 @@ def test_stream_variants_match_oracle(okz, orc, wpt, fuse, p, q, s_sel):
         assert (S1, S2) == ref.sums() and W2 == ref.width2()
 
 
+@pytest.mark.parametrize("kernel", STREAM_KINDS)
 @pytest.mark.parametrize("wpt,fuse", [(4, 2), (8, 2), (8, 1)])
-def test_stream_variants_long_run_L32768(okz, wpt, fuse):
+def test_stream_variants_long_run_L32768(okz, wpt, fuse, kernel):
     """Long runs at L = 2^15 (several CTA bands per SM) agree with the plain kernel."""
     L = 32768
-    a = okz.Simulation(L, 1.0, 0.0, seed=8, kernel=okz.OKZ_KERNEL_STREAM,
+    a = okz.Simulation(L, 1.0, 0.0, seed=8, kernel=kernel,
                        words_per_thread=wpt, sweeps_per_pass=fuse)
     b = okz.Simulation(L, 1.0, 0.0, seed=8, kernel=okz.OKZ_KERNEL_PLAIN)
     a.sweep(37)
@@ -106,10 +114,11 @@ def test_stream_variants_long_run_L32768(okz, wpt, fuse):
     b.close()
 
 
+@pytest.mark.parametrize("kernel", [2, 3, 4])
 @pytest.mark.parametrize("L", [4096, 8192, 16384])
-def test_stream_equals_plain_long_run(okz, L):
-    """Both kernels give identical lattices over many sweeps (no oracle needed)."""
-    a = okz.Simulation(L, 0.75, 0.25, seed=5, kernel=okz.OKZ_KERNEL_STREAM)
+def test_stream_equals_plain_long_run(okz, L, kernel):
+    """All kernels give identical lattices over many sweeps (no oracle needed)."""
+    a = okz.Simulation(L, 0.75, 0.25, seed=5, kernel=kernel)
     b = okz.Simulation(L, 0.75, 0.25, seed=5, kernel=okz.OKZ_KERNEL_PLAIN)
     for n in (10, 40):
         a.sweep(n)
@@ -122,7 +131,8 @@ def test_stream_equals_plain_long_run(okz, L):
     b.close()
 
 
-@pytest.mark.parametrize("L,kernel", [(64, 1), (256, 1), (4096, 2)])
+@pytest.mark.parametrize("L,kernel", [(64, 1), (256, 1), (4096, 2), (64, 3), (256, 3),
+                                      (4096, 4)])
 def test_moments_and_heights_match_oracle(okz, orc, L, kernel):
     ref = orc.Sim(L, 0.95, 0.05, 3)
     with okz.Simulation(L, 0.95, 0.05, seed=3, kernel=kernel) as sim:
@@ -139,19 +149,23 @@ def test_moments_and_heights_match_oracle(okz, orc, L, kernel):
         assert np.array_equal(sim.heights(y0=L // 2 - 3, ny=5), h[L // 2 - 3:L // 2 + 2])
 
 
-def test_flat_start_width(okz):
+@pytest.mark.parametrize("kernel", [0, 1, 2, 3, 4])
+def test_flat_start_width(okz, kernel):
     for L in (32, 256, 4096):
-        with okz.Simulation(L, 1.0, 0.0, seed=1) as sim:
+        if kernel in (2, 4) and L < 4096:
+            continue
+        with okz.Simulation(L, 1.0, 0.0, seed=1, kernel=kernel) as sim:
             S1, S2, W2 = sim.width2()
             assert W2 == 0.25 and S1 == L * L // 2 and S2 == L * L // 2
 
 
-def test_growth_series_L256(okz, orc):
+@pytest.mark.parametrize("kernel", PLAIN_KINDS)
+def test_growth_series_L256(okz, orc, kernel):
     """L = 256, p = 1, q = 0, seed 1, 1000 sweeps, W^2 at 20 log-spaced times:
     every record equal to the oracle's."""
     times = orc.sample_times(1000, 20)
     ref = orc.Sim(256, 1.0, 0.0, 1)
-    with okz.Simulation(256, 1.0, 0.0, seed=1) as sim:
+    with okz.Simulation(256, 1.0, 0.0, seed=1, kernel=kernel) as sim:
         for t in times:
             ref.sweep(t - ref.t)
             sim.sweep(t - sim.info().t)
@@ -162,7 +176,7 @@ def test_growth_series_L256(okz, orc):
 
 
 def test_checkpoint_resume_is_exact(okz):
-    for L, kernel in [(256, 1), (8192, 2)]:
+    for L, kernel in [(256, 1), (8192, 2), (256, 3), (8192, 4)]:
         a = okz.Simulation(L, 0.75, 0.25, seed=9, kernel=kernel)
         a.sweep(30)
         planes, H0, t = a.state()
@@ -175,6 +189,30 @@ def test_checkpoint_resume_is_exact(okz):
         assert np.array_equal(pa, pb) and (ha, ta) == (hb, tb) == (ha, 60)
         a.close()
         b.close()
+
+
+def test_restore_across_representations(okz, orc):
+    """A checkpoint taken from the slope planes resumes on the parity plane and
+    vice versa; an odd H0 is rejected (h(0,0) is even)."""
+    L = 8192
+    ref = orc.Sim(L, 0.75, 0.25, 12)
+    ref.sweep(20)
+    a = okz.Simulation(L, 0.75, 0.25, seed=12, kernel=okz.OKZ_KERNEL_STREAM)
+    a.sweep(10)
+    planes, H0, t = a.state()
+    b = okz.Simulation(L, 0.75, 0.25, seed=12, kernel=okz.OKZ_KERNEL_PARITY_STREAM)
+    b.restore(planes, H0, t)
+    b.sweep(5)
+    c = okz.Simulation(L, 0.75, 0.25, seed=12, kernel=okz.OKZ_KERNEL_PLAIN)
+    pb, hb, tb = b.state()
+    c.restore(pb, hb, tb)
+    c.sweep(5)
+    _compare(c, ref)
+    with pytest.raises(okz.OkzError) as e:
+        b.restore(planes, H0 + 1, t)
+    assert e.value.status == okz.OKZ_EINVAL
+    for sim in (a, b, c):
+        sim.close()
 
 
 def test_torch_buffer_and_stream(okz):
@@ -275,7 +313,7 @@ def test_full_size_L131072(okz, orc):
     import torch
     L, n, seed = 1 << 17, 8, 11
     with okz.Simulation(L, 1.0, 0.0, seed=seed) as sim:
-        assert sim.info().kernel == okz.OKZ_KERNEL_STREAM
+        assert sim.info().kernel == okz.OKZ_KERNEL_PARITY_STREAM
         sim.sweep(n)
         planes = torch.empty((2, L, L // 32), dtype=torch.int32, device="cuda")
         _, H0, t = sim.state(out=planes)
@@ -331,7 +369,7 @@ def test_growth_series_L16384_golden(okz):
         pytest.fail("golden series missing: run tests/golden/make_growth_golden.py")
     rows, digest = _golden_rows(path)
     with okz.Simulation(16384, 1.0, 0.0, seed=7) as sim:
-        assert sim.info().kernel == okz.OKZ_KERNEL_STREAM
+        assert sim.info().kernel == okz.OKZ_KERNEL_PARITY_STREAM
         for (t, H0, S1, S2, W2) in rows:
             sim.sweep(t - sim.info().t)
             s1, s2, w2 = sim.width2()
