@@ -202,6 +202,31 @@ okz_status okz_destroy(okz_sim *sim);
 /* Message of the calling thread's most recent failure ("" if none). */
 const char *okz_last_error(void);
 
+/* okz_width2_noalloc -- the paper has no counterpart to this entry point; it
+ * serves callers that cannot allocate device memory when they measure, e.g.
+ * because a framework's caching allocator already holds all free device
+ * memory, because an allocation (and the synchronisation it can cause) is not
+ * allowed on their latency-critical path, or because their policy forbids
+ * allocating after start-up.
+ *
+ * Computes the same exact sums and W^2 as okz_width2 for a state the caller
+ * owns: `planes` is a device pointer to the slope-plane layout above (X
+ * plane then Y plane), `H0` its h(0,0), `stream` the cudaStream_t to run on
+ * (NULL = the legacy default stream). 32 <= L <= 131072 and L % 32 == 0;
+ * a larger L is rejected with OKZ_EINVAL ("exceeds the fixed scratch size").
+ * Outputs as okz_width2; any may be NULL. Synchronizing: waits for `stream`.
+ *
+ * It allocates nothing (no cudaMalloc, cudaFree or pinned buffers). Its
+ * scratch is one fixed device array of 1 MiB + 129 KiB + 256 B, present on
+ * every device that loads this library until the process exits. The first
+ * call on a device looks up that array's address (cudaGetSymbolAddress, with
+ * the device current); make that first call before any stream capture. All
+ * calls share the one array: calls whose work overlaps on the GPU (different
+ * streams, or several host threads) race and return wrong sums -- serialise
+ * them. */
+okz_status okz_width2_noalloc(const uint32_t *planes, int64_t L, int64_t H0, void *stream,
+                              okz_i128 *S1, okz_i128 *S2, double *W2);
+
 /* Acceptance precision and thresholds for (p, q, s_sel, k_max), the rule
  * stated above; the host computation every simulation uses. */
 okz_status okz_thresholds(double p, double q, double s_sel, int32_t k_max,

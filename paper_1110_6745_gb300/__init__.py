@@ -75,6 +75,9 @@ _SIGS = {
     "okz_stream": (_vp, [_vp]),
     "okz_destroy": (_c.c_int, [_vp]),
     "okz_last_error": (_c.c_char_p, []),
+    "okz_width2_noalloc": (_c.c_int, [_vp, _c.c_int64, _c.c_int64, _vp,
+                                      _c.POINTER(okz_i128), _c.POINTER(okz_i128),
+                                      _c.POINTER(_c.c_double)]),
     "okz_thresholds": (_c.c_int, [_c.c_double, _c.c_double, _c.c_double, _c.c_int32,
                                   _c.POINTER(_c.c_int32), _c.POINTER(_c.c_uint64),
                                   _c.POINTER(_c.c_uint64)]),
@@ -205,6 +208,16 @@ def okz_restore(h, planes, H0, t):
         assert planes.is_contiguous()
         ptr, is_dev = planes.data_ptr(), int(planes.is_cuda)
     _check(lib().okz_restore(h, ptr, is_dev, int(H0), int(t)), "okz_restore")
+
+
+def okz_width2_noalloc(planes_dev_ptr, L, H0, stream=None):
+    """Exact (S1, S2, W2) of caller-owned device planes (slope layout), for
+    callers that cannot allocate device memory; uses a fixed scratch array
+    shared by all calls (serialise calls that could overlap on the GPU)."""
+    S1, S2, W2 = okz_i128(), okz_i128(), ctypes.c_double()
+    _check(lib().okz_width2_noalloc(planes_dev_ptr, int(L), int(H0), stream, ctypes.byref(S1),
+                                    ctypes.byref(S2), ctypes.byref(W2)), "okz_width2_noalloc")
+    return S1.value(), S2.value(), W2.value
 
 
 def okz_get_info(h):
