@@ -36,15 +36,25 @@ UNIT = "GUPS (1e9 site-update attempts/s)"
 BYTES_PER_SITE_LAUNCH = {"slope": 0.5, "parity": 0.25}
 KERNELS = {"auto": 0, "slope": 2, "parity": 4}
 
-# dram__bytes_read.sum + dram__bytes_write.sum of one sweep-kernel launch, taken
-# by ncu on an L = 32768 lattice and scaled by the site count to L = 2^17, for
-# the kernel source with this SHA-256 (None: not measured for this source).
-TRAFFIC_BYTES_PER_SITE = None
-TRAFFIC_SOURCE_SHA = None
+# Integer work of one sweep of the parity-plane kernel, per site (the ALU roof):
+# per 32-site word and half-sweep 2 funnel shifts + 4 three-input logic ops +
+# 1 xor = 7 ALU-pipe ops; per 128-site Philox4x32-10 block 20 three-input xors
+# (ALU pipe) and 20 32x32->64 multiplies (FMA pipe).
+ALU_OPS_PER_SITE_SWEEP = {"parity": 2 * 7 / 32 + 20 / 128,
+                          "slope": 2 * 9 / 32 + 20 / 128}
+ALU_LANES_PER_SM = 64  # INT32 ALU-pipe lanes per SM per clock (16 per sub-partition)
+N_SMS = 152
+
+# dram__bytes_read.sum + dram__bytes_write.sum of one sweep-kernel launch (ncu,
+# L = 65536, 2 sweeps per launch), per site; valid only for the kernel source
+# with this SHA-256 (traffic is reported as null once the source changes).
+TRAFFIC_BYTES_PER_SITE = {"parity": 1046466560 / 65536 ** 2}
+TRAFFIC_SOURCE_SHA = {"parity": "4cfe1f0cbbbd477d488b342b8850e8bdd3662fd1e09e5863e5a27a24588c0752"}
+KERNEL_SOURCE = {"parity": "parity.cu", "slope": "sweep_stream.cu"}
 
 
-def _kernel_sha():
-    p = os.path.join(ROOT, "paper_1110_6745_gb300", "csrc", "sweep_stream.cu")
+def _kernel_sha(repr_name):
+    p = os.path.join(ROOT, "paper_1110_6745_gb300", "csrc", KERNEL_SOURCE[repr_name])
     return hashlib.sha256(open(p, "rb").read()).hexdigest()
 
 
@@ -251,8 +261,15 @@ def run_gpu(args, world, rank, local):
     achieved = alg_bytes / per_launch_s / 1e9
     peak, peak_kind = _peaks()
     traffic = None
-    if TRAFFIC_BYTES_PER_SITE is not None and TRAFFIC_SOURCE_SHA == _kernel_sha():
-        traffic = TRAFFIC_BYTES_PER_SITE * N
+    if (repr_name in TRAFFIC_BYTES_PER_SITE
+            and TRAFFIC_SOURCE_SHA.get(repr_name) == _kernel_sha(repr_name)):
+        traffic = TRAFFIC_BYTES_PER_SITE[repr_name] * N
+    # ALU roof: algorithmic ALU-pipe ops per launch / launch time, against
+    # 152 SMs x 64 lanes x the SM clock sampled during the timed region
+    sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
+    alu_peak = N_SMS * ALU_LANES_PER_SM * sm_mhz * 1e6 / 1e12
+    alu_ops = ALU_OPS_PER_SITE_SWEEP[repr_name] * N * fuse
+    alu_achieved = alu_ops / per_launch_s / 1e12
 
     # end to end through the C-ABI with host buffers: each step restores the
     # lattice from pinned host memory, sweeps, and reads back the exact sums
@@ -286,13 +303,17 @@ def run_gpu(args, world, rank, local):
                    "L": L, "sweeps_per_step": SWEEPS_PER_STEP, "t_range": [0, sweeps],
                    "l2": "inputs larger than L2 (2 x 4 GiB ping-pong planes)",
                    "parallelism": "replicas" if world > 1 else "single"},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic,
+        "roofline": {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak,
+                     "unit": "Tops/s", "frac": alu_achieved / alu_peak,
+                     "traffic": traffic,
                      "kernel": ("parity_stream_kernel" if repr_name == "parity"
                                 else "sweep_stream_kernel"),
-                     "peak_kind": peak_kind, "bytes_per_launch": alg_bytes,
-                     "sweeps_per_launch": fuse, "words_per_thread": wpt,
-                     "launch_ms": per_launch_s * 1e3},
+                     "peak_kind": "derived: 152 SMs x 64 INT32 lanes x sampled SM clock",
+                     "ops_per_launch": alu_ops, "sweeps_per_launch": fuse,
+                     "words_per_thread": wpt, "launch_ms": per_launch_s * 1e3},
+        "roofline_hbm": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "bytes_per_launch": alg_bytes, "peak_kind": peak_kind},
         "sweep_gups": N * fuse / per_launch_s / 1e9,
         "slope_roofline_frac": (N * fuse / per_launch_s) * 0.5 / (peak * 1e9),
         "gpu_launches": launches,
