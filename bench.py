@@ -327,6 +327,93 @@ def run_gpu(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def replica_mix(n=4096, seed=2026):
+    """The batched workload: L_r = 2^e_r, e_r ~ U{6..11} (PCG64), p = 0.95, q = 0.05,
+    seed_r = 1000 + r, full budgets T_r = ceil(4 L_r^1.61) sweeps."""
+    import numpy as np
+    rng = np.random.Generator(np.random.PCG64(seed))
+    e = rng.integers(6, 12, size=n)
+    L = (1 << e).astype(np.int64)
+    T = np.ceil(4 * L.astype(np.float64) ** 1.61).astype(np.int64)
+    seeds = (1000 + np.arange(n)).astype(np.uint64)
+    return L, T, seeds
+
+
+def run_batched(args, world, rank, local):
+    """4096 independent replicas in one graph-captured persistent launch, against
+    per-replica launches of the plain kernel on the same GPU."""
+    import numpy as np
+    import torch
+
+    import paper_1110_6745_gb300 as okz
+
+    torch.cuda.set_device(local)
+    L, T, seeds = replica_mix()
+    n = len(L)
+    frac = args.budget_frac
+    budgets = np.maximum(1, T // frac)
+    small = np.maximum(1, T // args.baseline_frac)
+
+    def batched(sw):
+        b = okz.Batch(L, [0.95] * n, [0.05] * n, [int(x) + rank for x in seeds])
+        b.autotune(probe_sweeps=2)
+        st = torch.cuda.ExternalStream(b.stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        _barrier(world)
+        e0.record(st)
+        b.run(sw)
+        b.sync()
+        W2, sk, ku = b.stats()
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        tiling = b.tiling()
+        b.close()
+        return ms, W2, tiling
+
+    ms, W2, tiling = batched(budgets)
+    ms = _max_over_ranks(world, ms)
+    attempts = float(np.sum(L.astype(np.float64) ** 2 * budgets))
+    value = world * attempts / (ms / 1e3) / 1e9
+    ms_small, _, _ = batched(small)
+    batched_small = float(np.sum(L.astype(np.float64) ** 2 * small)) / (ms_small / 1e3) / 1e9
+
+    # per-replica launches of the plain (parity-plane, in-place) kernel
+    sims = [okz.Simulation(int(L[r]), 0.95, 0.05, seed=int(seeds[r]) + rank,
+                           kernel=okz.OKZ_KERNEL_PARITY_PLAIN) for r in range(n)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for r in range(n):
+        sims[r].sweep(int(small[r]))
+        sims[r].synchronize()
+    plain_s = time.perf_counter() - t0
+    plain = float(np.sum(L.astype(np.float64) ** 2 * small)) / plain_s / 1e9
+    check = [int(r) for r in np.argsort(L)[:: n // 16]]
+    for s_ in sims:
+        s_.close()
+    if rank != 0:
+        return
+    line = {
+        "metric": "aggregate site-update attempts/s, batched replicas", "value": value,
+        "unit": UNIT, "n_gpus": world, "steps": 1, "warmup": 0, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic", "impl": "okz-batch",
+        "config": {"workload": "4096 replicas, L = 2^e, e ~ U{6..11} (PCG64 2026), p=0.95 "
+                               "q=0.05 s_sel=1/2, seeds 1000+r, striped start, budgets "
+                               "ceil(4 L^1.61)/%d sweeps; final W^2, skewness, kurtosis" % frac,
+                   "replicas": n, "attempts": attempts,
+                   "tiling": {"threads": tiling[0], "smem_bytes": tiling[1], "grid": tiling[2]}},
+        "per_replica_plain": {"value": plain, "unit": UNIT,
+                              "budgets": "ceil(4 L^1.61)/%d" % args.baseline_frac,
+                              "kernel": "parity plain, one okz_sim per replica, sequential"},
+        "batched_same_budgets": {"value": batched_small, "unit": UNIT},
+        "batched_over_plain": batched_small / plain,
+        "w2_mean_by_L": {int(l): float(np.nanmean(W2[L == l])) for l in np.unique(L)},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -338,10 +425,20 @@ def main():
     ap.add_argument("--kernel", default="auto", choices=sorted(KERNELS))
     ap.add_argument("--wpt", type=int, default=0, help="words per thread (0 = library choice)")
     ap.add_argument("--fuse", type=int, default=0, help="sweeps per launch (0 = library choice)")
+    ap.add_argument("--workload", default="growth", choices=["growth", "batched", "served"])
+    ap.add_argument("--budget-frac", type=int, default=64,
+                    help="batched: run ceil(4 L^1.61)/frac sweeps per replica")
+    ap.add_argument("--baseline-frac", type=int, default=2048,
+                    help="batched: budgets of the per-replica comparison")
     args = ap.parse_args()
     world, rank, local = _dist_init(args)
     if args.impl == "reference":
         run_reference(args, world, rank)
+    elif args.workload == "batched":
+        run_batched(args, world, rank, local)
+    elif args.workload == "served":
+        from paper_1110_6745_gb300 import serve
+        serve.bench(args, world, rank, local, UNIT)
     else:
         run_gpu(args, world, rank, local)
     if world > 1:

@@ -227,6 +227,86 @@ const char *okz_last_error(void);
 okz_status okz_width2_noalloc(const uint32_t *planes, int64_t L, int64_t H0, void *stream,
                               okz_i128 *S1, okz_i128 *S2, double *W2);
 
+/* ---------------------------------------------------------------------------
+ * Batched and pooled lattices (Sec. III: many independent runs per size).
+ *
+ * An okz_batch is a slot table of independent lattices (32 <= L <= 8192,
+ * L % 32 == 0) kept on the device as height-parity planes in one arena.
+ * okz_batch_run advances any subset of slots by per-slot sweep counts in one
+ * persistent kernel launch (a CUDA graph replayed each run): CTAs take
+ * (slot, sweeps) items longest-first from a device queue, stage a lattice in
+ * shared memory when it fits, and sweep it in place. Every slot evolves
+ * bit-identically to an okz_sim with the same (L, p, q, seed, s_sel, k_max).
+ * --------------------------------------------------------------------------- */
+typedef struct okz_batch okz_batch;
+
+/* An empty slot table: `arena_bytes` of device memory for lattices
+ * (L*L/8 bytes each, 256-byte granules), `max_slots` slots, selection
+ * probability and acceptance precision shared by all slots, `stream` a
+ * cudaStream_t (NULL = own stream). Errors: EINVAL, ENOMEM, ECUDA. */
+okz_status okz_pool_create(size_t arena_bytes, int32_t max_slots, double s_sel,
+                           int32_t k_max, void *stream, okz_batch **out);
+
+/* n slots with the given sizes, probabilities and seeds (s_sel = 0.5,
+ * k_max = 32), each at the striped start; slot i is replica i. */
+okz_status okz_batch_create(int32_t n, const int64_t *L, const double *p, const double *q,
+                            const uint64_t *seed, okz_batch **out);
+
+/* Admits a lattice into a free slot (striped start, t = 0, H0 = 0).
+ * Synchronizing. Errors: EBUSY (no free slot or no arena space -- the caller
+ * may retry after removing slots), EINVAL, EUNSUPPORTED. */
+okz_status okz_batch_add(okz_batch *b, int64_t L, double p, double q, uint64_t seed,
+                         int32_t *slot);
+
+/* Frees a slot and its arena space. Synchronizing. */
+okz_status okz_batch_remove(okz_batch *b, int32_t slot);
+
+/* Advances slot i by sweeps[i] sweeps (array of max_slots entries; 0 = leave
+ * the slot alone) in one launch on the batch's stream and returns without
+ * waiting for it (it waits for the previous run first). Errors: EINVAL
+ * (negative count or an empty slot with work), EOVERFLOW, ECUDA. */
+okz_status okz_batch_run(okz_batch *b, const int64_t *sweeps);
+
+/* Waits for the batch's stream. */
+okz_status okz_batch_sync(okz_batch *b);
+
+/* Synchronizing. Per slot (arrays of max_slots entries; NaN for empty slots):
+ * W^2 of Eq. (4) from exact sums, and the skewness and excess kurtosis of
+ * the heights (formulas of okz_moments). Any pointer may be NULL. */
+okz_status okz_batch_stats(okz_batch *b, double *W2, double *skew, double *kurt);
+
+/* Synchronizing. Exact S_n = sum (h - H0)^n, n = 1..4, H0 and t of a slot. */
+okz_status okz_batch_sums(okz_batch *b, int32_t slot, okz_i128 Sk[4], int64_t *H0,
+                          uint64_t *t);
+
+/* Synchronizing. Exact sums of n listed slots in one launch: Sk[4*j + m] =
+ * S_{m+1} of slots[j], H0[j], t[j] (any output may be NULL). */
+okz_status okz_batch_measure(okz_batch *b, int32_t n, const int32_t *slots, okz_i128 *Sk,
+                             int64_t *H0, uint64_t *t);
+
+/* Synchronizing. The slot's state as slope planes (layout above) in host
+ * memory (2*L*L/8 bytes), H0 and t. */
+okz_status okz_batch_state(okz_batch *b, int32_t slot, uint32_t *planes_out, int64_t *H0,
+                           uint64_t *t);
+
+/* Launch shape of okz_batch_run: threads per CTA (256, 512 or 1024) and the
+ * shared-memory staging size (lattices up to that many bytes are swept in
+ * shared memory). Results do not depend on it. */
+okz_status okz_batch_set_tiling(okz_batch *b, int32_t threads, size_t smem_bytes);
+okz_status okz_batch_get_tiling(okz_batch *b, int32_t *threads, size_t *smem_bytes,
+                                int32_t *grid);
+
+/* Times every tiling on a scratch copy of the slot mix (fresh lattices,
+ * probe_sweeps sweeps each) and keeps the fastest. Synchronizing; the
+ * batch's own lattices are untouched. */
+okz_status okz_batch_autotune(okz_batch *b, int32_t probe_sweeps);
+
+/* The batch's stream (a cudaStream_t). */
+void *okz_batch_stream(okz_batch *b);
+
+/* Waits for outstanding work and frees everything. NULL is accepted. */
+okz_status okz_batch_destroy(okz_batch *b);
+
 /* Acceptance precision and thresholds for (p, q, s_sel, k_max), the rule
  * stated above; the host computation every simulation uses. */
 okz_status okz_thresholds(double p, double q, double s_sel, int32_t k_max,

@@ -78,6 +78,26 @@ _SIGS = {
     "okz_width2_noalloc": (_c.c_int, [_vp, _c.c_int64, _c.c_int64, _vp,
                                       _c.POINTER(okz_i128), _c.POINTER(okz_i128),
                                       _c.POINTER(_c.c_double)]),
+    "okz_pool_create": (_c.c_int, [_c.c_size_t, _c.c_int32, _c.c_double, _c.c_int32, _vp,
+                                   _c.POINTER(_vp)]),
+    "okz_batch_create": (_c.c_int, [_c.c_int32, _vp, _vp, _vp, _vp, _c.POINTER(_vp)]),
+    "okz_batch_add": (_c.c_int, [_vp, _c.c_int64, _c.c_double, _c.c_double, _c.c_uint64,
+                                 _c.POINTER(_c.c_int32)]),
+    "okz_batch_remove": (_c.c_int, [_vp, _c.c_int32]),
+    "okz_batch_run": (_c.c_int, [_vp, _vp]),
+    "okz_batch_sync": (_c.c_int, [_vp]),
+    "okz_batch_stats": (_c.c_int, [_vp, _vp, _vp, _vp]),
+    "okz_batch_sums": (_c.c_int, [_vp, _c.c_int32, _c.POINTER(okz_i128),
+                                  _c.POINTER(_c.c_int64), _c.POINTER(_c.c_uint64)]),
+    "okz_batch_measure": (_c.c_int, [_vp, _c.c_int32, _vp, _vp, _vp, _vp]),
+    "okz_batch_state": (_c.c_int, [_vp, _c.c_int32, _vp, _c.POINTER(_c.c_int64),
+                                   _c.POINTER(_c.c_uint64)]),
+    "okz_batch_set_tiling": (_c.c_int, [_vp, _c.c_int32, _c.c_size_t]),
+    "okz_batch_get_tiling": (_c.c_int, [_vp, _c.POINTER(_c.c_int32), _c.POINTER(_c.c_size_t),
+                                        _c.POINTER(_c.c_int32)]),
+    "okz_batch_autotune": (_c.c_int, [_vp, _c.c_int32]),
+    "okz_batch_stream": (_vp, [_vp]),
+    "okz_batch_destroy": (_c.c_int, [_vp]),
     "okz_thresholds": (_c.c_int, [_c.c_double, _c.c_double, _c.c_double, _c.c_int32,
                                   _c.POINTER(_c.c_int32), _c.POINTER(_c.c_uint64),
                                   _c.POINTER(_c.c_uint64)]),
@@ -301,6 +321,187 @@ class Simulation:
             okz_destroy(self.h)
             self.h = None
             self._buf = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------------------
+# Batched and pooled lattices
+# ---------------------------------------------------------------------------
+def okz_pool_create(arena_bytes, max_slots, s_sel=0.5, k_max=32, stream=None):
+    h = ctypes.c_void_p()
+    _check(lib().okz_pool_create(int(arena_bytes), int(max_slots), float(s_sel), int(k_max),
+                                 stream, ctypes.byref(h)), "okz_pool_create")
+    return h
+
+
+def okz_batch_create(L, p, q, seed):
+    n = len(L)
+    La = np.ascontiguousarray(L, np.int64)
+    pa = np.ascontiguousarray(p, np.float64)
+    qa = np.ascontiguousarray(q, np.float64)
+    sa = np.ascontiguousarray(seed, np.uint64)
+    h = ctypes.c_void_p()
+    _check(lib().okz_batch_create(n, La.ctypes.data, pa.ctypes.data, qa.ctypes.data,
+                                  sa.ctypes.data, ctypes.byref(h)), "okz_batch_create")
+    return h
+
+
+def okz_batch_add(b, L, p, q, seed):
+    slot = ctypes.c_int32()
+    _check(lib().okz_batch_add(b, int(L), float(p), float(q), int(seed), ctypes.byref(slot)),
+           "okz_batch_add")
+    return slot.value
+
+
+def okz_batch_remove(b, slot):
+    _check(lib().okz_batch_remove(b, int(slot)), "okz_batch_remove")
+
+
+def okz_batch_run(b, sweeps):
+    sw = np.ascontiguousarray(sweeps, np.int64)
+    _check(lib().okz_batch_run(b, sw.ctypes.data), "okz_batch_run")
+
+
+def okz_batch_sync(b):
+    _check(lib().okz_batch_sync(b), "okz_batch_sync")
+
+
+def okz_batch_stats(b, max_slots):
+    W2 = np.empty(max_slots, np.float64)
+    sk = np.empty(max_slots, np.float64)
+    ku = np.empty(max_slots, np.float64)
+    _check(lib().okz_batch_stats(b, W2.ctypes.data, sk.ctypes.data, ku.ctypes.data),
+           "okz_batch_stats")
+    return W2, sk, ku
+
+
+def okz_batch_sums(b, slot):
+    Sk = (okz_i128 * 4)()
+    H0, t = ctypes.c_int64(), ctypes.c_uint64()
+    _check(lib().okz_batch_sums(b, int(slot), Sk, ctypes.byref(H0), ctypes.byref(t)),
+           "okz_batch_sums")
+    return [s.value() for s in Sk], H0.value, t.value
+
+
+def okz_batch_measure(b, slots):
+    """Exact sums of the listed slots in one launch -> [(Sk[4], H0, t)]."""
+    n = len(slots)
+    if n == 0:
+        return []
+    sl = np.ascontiguousarray(slots, np.int32)
+    Sk = (okz_i128 * (4 * n))()
+    H0 = np.empty(n, np.int64)
+    t = np.empty(n, np.uint64)
+    _check(lib().okz_batch_measure(b, n, sl.ctypes.data, Sk, H0.ctypes.data, t.ctypes.data),
+           "okz_batch_measure")
+    return [([Sk[4 * j + m].value() for m in range(4)], int(H0[j]), int(t[j])) for j in range(n)]
+
+
+def okz_batch_state(b, slot, L):
+    out = np.empty((2, int(L), int(L) // 32), np.uint32)
+    H0, t = ctypes.c_int64(), ctypes.c_uint64()
+    _check(lib().okz_batch_state(b, int(slot), out.ctypes.data, ctypes.byref(H0),
+                                 ctypes.byref(t)), "okz_batch_state")
+    return out, H0.value, t.value
+
+
+def okz_batch_set_tiling(b, threads, smem_bytes):
+    _check(lib().okz_batch_set_tiling(b, int(threads), int(smem_bytes)), "okz_batch_set_tiling")
+
+
+def okz_batch_get_tiling(b):
+    th, sm, gr = ctypes.c_int32(), ctypes.c_size_t(), ctypes.c_int32()
+    _check(lib().okz_batch_get_tiling(b, ctypes.byref(th), ctypes.byref(sm), ctypes.byref(gr)),
+           "okz_batch_get_tiling")
+    return th.value, sm.value, gr.value
+
+
+def okz_batch_autotune(b, probe_sweeps=8):
+    _check(lib().okz_batch_autotune(b, int(probe_sweeps)), "okz_batch_autotune")
+
+
+def okz_batch_stream(b):
+    return lib().okz_batch_stream(b)
+
+
+def okz_batch_destroy(b):
+    _check(lib().okz_batch_destroy(b), "okz_batch_destroy")
+
+
+class Batch:
+    """Owning wrapper of an okz_batch slot table."""
+
+    def __init__(self, L=None, p=None, q=None, seed=None, arena_bytes=None, max_slots=None,
+                 s_sel=0.5, k_max=32, stream=None):
+        if L is not None:
+            self.h = okz_batch_create(L, p, q, seed)
+            self.max_slots = len(L)
+            self.L = {i: int(l) for i, l in enumerate(L)}
+        else:
+            self.h = okz_pool_create(arena_bytes, max_slots, s_sel, k_max, stream)
+            self.max_slots = int(max_slots)
+            self.L = {}
+
+    def add(self, L, p, q, seed):
+        slot = okz_batch_add(self.h, L, p, q, seed)
+        self.L[slot] = int(L)
+        return slot
+
+    def remove(self, slot):
+        okz_batch_remove(self.h, slot)
+        self.L.pop(slot, None)
+
+    def run(self, sweeps):
+        if isinstance(sweeps, dict):
+            arr = np.zeros(self.max_slots, np.int64)
+            for k, v in sweeps.items():
+                arr[k] = v
+            sweeps = arr
+        okz_batch_run(self.h, sweeps)
+
+    def sync(self):
+        okz_batch_sync(self.h)
+
+    def stats(self):
+        return okz_batch_stats(self.h, self.max_slots)
+
+    def sums(self, slot):
+        return okz_batch_sums(self.h, slot)
+
+    def state(self, slot):
+        return okz_batch_state(self.h, slot, self.L[slot])
+
+    def measure(self, slots):
+        return okz_batch_measure(self.h, list(slots))
+
+    def set_tiling(self, threads, smem_bytes):
+        okz_batch_set_tiling(self.h, threads, smem_bytes)
+
+    def tiling(self):
+        return okz_batch_get_tiling(self.h)
+
+    def autotune(self, probe_sweeps=8):
+        okz_batch_autotune(self.h, probe_sweeps)
+
+    @property
+    def stream(self):
+        return okz_batch_stream(self.h)
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            okz_batch_destroy(self.h)
+            self.h = None
 
     def __enter__(self):
         return self

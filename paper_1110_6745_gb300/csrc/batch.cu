@@ -1,0 +1,331 @@
+// batch.cu -- many independent lattices ("slots") in one persistent launch.
+//
+// Replicas are the paper's parallelism across independent runs (Kelling &
+// Odor, arXiv:1110.6745, Sec. III: 10-1000 independent simulations per size).
+// Every slot holds one height-parity plane (parity.cu) in a device arena. A
+// launch drains a device work queue of (slot, sweeps) items: one CTA takes an
+// item, stages the lattice in shared memory when it fits (else works on it in
+// global memory, where a 2^11 lattice stays L2-resident), runs the sweeps in
+// place -- a half-sweep updates only one sublattice and a move toggles only
+// the site's own bit, so a CTA barrier between half-sweeps is the only
+// synchronisation -- and writes the lattice, t and H0 back. Random draws use
+// the slot's own seed with the single-lattice counter layout, so every slot
+// evolves bit-identically to a simulation of its own.
+#include <cuda_runtime.h>
+
+#include "okz_batch_internal.h"
+
+namespace okz {
+
+namespace {
+
+// One 128-site group (4 words) of half-sweep s, in place on B.
+template <bool LAZY>
+__device__ __forceinline__ void group_update(uint32_t *B, int L, int W, uint32_t g, int s,
+                                             uint32_t t, uint64_t seed, const Accept &acc,
+                                             int &dH0) {
+  uint32_t mn[4], mx[4], ctr[4];
+  uint32_t idx[4];
+  const uint32_t S = s ? ~0u : 0u;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const uint32_t gw = 4 * g + j;
+    const uint32_t y = gw / (uint32_t)W, w = gw - y * (uint32_t)W;
+    const uint32_t wl = (w == 0) ? W - 1 : w - 1, wr = (w == (uint32_t)W - 1) ? 0 : w + 1;
+    const uint32_t yd = (y == 0) ? L - 1 : y - 1, yu = (y == (uint32_t)L - 1) ? 0 : y + 1;
+    idx[j] = gw;
+    ctr[j] = B[gw];
+    const uint32_t l = __funnelshift_l(B[y * W + wl], ctr[j], 1);
+    const uint32_t r = __funnelshift_r(ctr[j], B[y * W + wr], 1);
+    const uint32_t c = ctr[j] ^ S, d = B[yd * W + w], u = B[yu * W + w];
+    const uint32_t dl = l ^ c, dr = r ^ c, dd = d ^ c, du = u ^ c;
+    const uint32_t a = active_mask(y, s);
+    mn[j] = a & ~(dl | dr | dd | du);
+    mx[j] = a & dl & dr & dd & du;
+  }
+  const uint64_t full = 1ull << acc.k;
+  uint32_t ltp[4], eqp[4], ltq[4], eqq[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    ltp[j] = (acc.P >= full) ? mn[j] : 0u;
+    eqp[j] = (acc.P >= full || acc.P == 0) ? 0u : mn[j];
+    ltq[j] = (acc.Q >= full) ? mx[j] : 0u;
+    eqq[j] = (acc.Q >= full || acc.Q == 0) ? 0u : mx[j];
+  }
+  for (int m = 0; m < acc.k; ++m) {
+    if (((eqp[0] | eqq[0]) | (eqp[1] | eqq[1]) | (eqp[2] | eqq[2]) | (eqp[3] | eqq[3])) == 0u)
+      break;
+    const u32x4 rb = group_bits((uint64_t)g, t, (uint32_t)m, seed);
+    const uint32_t pb = (uint32_t)(acc.P >> (acc.k - 1 - m)) & 1u;
+    const uint32_t qb = (uint32_t)(acc.Q >> (acc.k - 1 - m)) & 1u;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      lt_step(rb.v[j], pb, ltp[j], eqp[j]);
+      lt_step(rb.v[j], qb, ltq[j], eqq[j]);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const uint32_t f = ltp[j] | ltq[j];
+    if (f != 0u) B[idx[j]] = ctr[j] ^ f;
+    if (idx[j] == 0 && (f & 1u)) dH0 += (mn[0] & 1u) ? 2 : -2;  // site (0,0)
+  }
+}
+
+// Acceptance of 4 words (lazy, bit-sliced U < P / U < Q) -> flips.
+__device__ __forceinline__ void accept4(const uint32_t mn[4], const uint32_t mx[4], uint32_t g,
+                                        uint32_t t, uint64_t seed, const Accept &acc,
+                                        uint32_t f[4]) {
+  const uint64_t full = 1ull << acc.k;
+  uint32_t ltp[4], eqp[4], ltq[4], eqq[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    ltp[j] = (acc.P >= full) ? mn[j] : 0u;
+    eqp[j] = (acc.P >= full || acc.P == 0) ? 0u : mn[j];
+    ltq[j] = (acc.Q >= full) ? mx[j] : 0u;
+    eqq[j] = (acc.Q >= full || acc.Q == 0) ? 0u : mx[j];
+  }
+  for (int m = 0; m < acc.k; ++m) {
+    if (((eqp[0] | eqq[0]) | (eqp[1] | eqq[1]) | (eqp[2] | eqq[2]) | (eqp[3] | eqq[3])) == 0u)
+      break;
+    const u32x4 rb = group_bits((uint64_t)g, t, (uint32_t)m, seed);
+    const uint32_t pb = (uint32_t)(acc.P >> (acc.k - 1 - m)) & 1u;
+    const uint32_t qb = (uint32_t)(acc.Q >> (acc.k - 1 - m)) & 1u;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      lt_step(rb.v[j], pb, ltp[j], eqp[j]);
+      lt_step(rb.v[j], qb, ltq[j], eqq[j]);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) f[j] = ltp[j] | ltq[j];
+}
+
+// A group of 4 words inside one row (L % 128 == 0): 3 vector loads (row,
+// row below, row above), 2 neighbour words, 1 vector store. Whole-word
+// stores are safe: every bit another thread reads from these words sits on a
+// site this half-sweep does not move.
+template <bool POW2>
+__device__ __forceinline__ void row_group_update(uint32_t *B, int L, int W, uint32_t gpr,
+                                                 int lg_gpr, uint32_t g, int s, uint32_t t,
+                                                 uint64_t seed, const Accept &acc, int &dH0) {
+  const uint32_t y = POW2 ? (g >> lg_gpr) : (g / gpr);
+  const uint32_t w0 = 4 * (g - y * gpr);
+  const uint32_t yd = (y == 0) ? L - 1 : y - 1, yu = (y == (uint32_t)L - 1) ? 0 : y + 1;
+  uint32_t *row = B + (size_t)y * W;
+  const uint4 cv = *(const uint4 *)(row + w0);
+  const uint4 dv = *(const uint4 *)(B + (size_t)yd * W + w0);
+  const uint4 uv = *(const uint4 *)(B + (size_t)yu * W + w0);
+  const uint32_t lw = row[w0 == 0 ? W - 1 : w0 - 1];
+  const uint32_t rw = row[w0 + 4 == (uint32_t)W ? 0 : w0 + 4];
+  const uint32_t c[4] = {cv.x, cv.y, cv.z, cv.w};
+  const uint32_t d[4] = {dv.x, dv.y, dv.z, dv.w};
+  const uint32_t u[4] = {uv.x, uv.y, uv.z, uv.w};
+  const uint32_t S = s ? ~0u : 0u;
+  const uint32_t a = active_mask(y, s);
+  uint32_t mn[4], mx[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const uint32_t l = __funnelshift_l(j == 0 ? lw : c[j - 1], c[j], 1);
+    const uint32_t r = __funnelshift_r(c[j], j == 3 ? rw : c[j + 1], 1);
+    const uint32_t cc = c[j] ^ S;
+    const uint32_t dl = l ^ cc, dr = r ^ cc, dd = d[j] ^ cc, du = u[j] ^ cc;
+    mn[j] = a & ~(dl | dr | dd | du);
+    mx[j] = a & dl & dr & dd & du;
+  }
+  uint32_t f[4];
+  accept4(mn, mx, g, t, seed, acc, f);
+  if ((f[0] | f[1] | f[2] | f[3]) != 0u)
+    *(uint4 *)(row + w0) = make_uint4(c[0] ^ f[0], c[1] ^ f[1], c[2] ^ f[2], c[3] ^ f[3]);
+  if (g == 0 && (f[0] & 1u)) dH0 += (mn[0] & 1u) ? 2 : -2;  // site (0,0)
+}
+
+// `n` sweeps of one lattice by the whole CTA.
+__device__ __forceinline__ void cta_sweeps(uint32_t *B, int L, uint32_t t0, int n, uint64_t seed,
+                                           const Accept &acc, int &dH0) {
+  const int W = L >> 5;
+  const uint32_t groups = (uint32_t)L * (uint32_t)W / 4;
+  if ((L & 127) == 0) {  // groups never straddle rows
+    const uint32_t gpr = (uint32_t)W / 4;
+    const bool pow2 = (gpr & (gpr - 1)) == 0;
+    const int lg = __ffs(gpr) - 1;
+    for (int i = 0; i < n; ++i) {
+      const uint32_t t = t0 + (uint32_t)i;
+      for (int s = 0; s < 2; ++s) {
+        if (pow2) {
+          for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x)
+            row_group_update<true>(B, L, W, gpr, lg, g, s, t, seed, acc, dH0);
+        } else {
+          for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x)
+            row_group_update<false>(B, L, W, gpr, lg, g, s, t, seed, acc, dH0);
+        }
+        __syncthreads();
+      }
+    }
+    return;
+  }
+  for (int i = 0; i < n; ++i) {  // L = 32, 64, 96: groups span rows
+    const uint32_t t = t0 + (uint32_t)i;
+    for (int s = 0; s < 2; ++s) {
+      for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x)
+        group_update<true>(B, L, W, g, s, t, seed, acc, dH0);
+      __syncthreads();
+    }
+  }
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(1024, 1)
+batch_sweep_kernel(uint32_t *__restrict__ arena, SlotDesc *__restrict__ slots,
+                   const WorkTable *__restrict__ work, unsigned int *__restrict__ head,
+                   uint32_t smem_words) {
+  extern __shared__ __align__(16) uint32_t sm[];
+  __shared__ int item;
+  const int nwork = work->count;
+  while (true) {
+    if (threadIdx.x == 0) item = (int)atomicAdd(head, 1u);
+    __syncthreads();
+    const int it = item;
+    __syncthreads();
+    if (it >= nwork) break;
+    const int slot = work->item[it].slot;
+    const int n = work->item[it].sweeps;
+    SlotDesc d = slots[slot];
+    const uint32_t words = (uint32_t)d.L * (uint32_t)(d.L >> 5);
+    uint32_t *g = arena + d.offset_words;
+    Accept acc;
+    acc.P = d.P;
+    acc.Q = d.Q;
+    acc.k = d.k;
+    int dH0 = 0;
+    if (words <= smem_words) {
+      for (uint32_t w = threadIdx.x; w < words; w += blockDim.x) sm[w] = g[w];
+      __syncthreads();
+      cta_sweeps(sm, d.L, d.t, n, d.seed, acc, dH0);
+      for (uint32_t w = threadIdx.x; w < words; w += blockDim.x) g[w] = sm[w];
+    } else {
+      cta_sweeps(g, d.L, d.t, n, d.seed, acc, dH0);
+    }
+    if (threadIdx.x == 0) {  // thread 0 owns group 0, the only group with site (0,0)
+      slots[slot].t = d.t + (uint32_t)n;
+      slots[slot].H0 = d.H0 + dH0;
+    }
+    __syncthreads();
+  }
+}
+
+// Exact power sums S_1..S_4 of (h - H0) per slot: one CTA per slot item, a
+// warp per row (lanes own contiguous words), slopes formed from the parity
+// plane, 128-bit accumulation; results to the slot's sums.
+__global__ void __launch_bounds__(256)
+batch_moments_kernel(const uint32_t *__restrict__ arena, SlotDesc *__restrict__ slots,
+                     const WorkTable *__restrict__ work) {
+  __shared__ __int128 red[4][8];
+  extern __shared__ long long colh[];  // L entries
+  const int it = blockIdx.x;
+  if (it >= work->count) return;
+  const int slot = work->item[it].slot;
+  const SlotDesc d = slots[slot];
+  const int L = d.L, W = L >> 5;
+  const uint32_t *B = arena + d.offset_words;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // column 0 heights (relative to H0): sigma_y(0,y) = +1 iff b(0,y+1)^b(0,y)^p == 0
+  if (tid == 0) {
+    long long h = 0;
+    for (int y = 0; y < L; ++y) {
+      colh[y] = h;
+      const int yu = (y == L - 1) ? 0 : y + 1;
+      const uint32_t up = ~(B[y * W] ^ B[yu * W] ^ (uint32_t)(y & 1)) & 1u;
+      h += 2 * (long long)up - 1;
+    }
+  }
+  __syncthreads();
+  __int128 s[4] = {0, 0, 0, 0};
+  const int wpl = (W + 31) >> 5;
+  const int w0 = lane * wpl < W ? lane * wpl : W;
+  const int w1 = w0 + wpl < W ? w0 + wpl : W;
+  for (int y = warp; y < L; y += blockDim.x >> 5) {
+    const uint32_t *row = B + y * W;
+    const uint32_t P = (y & 1) ? 0x55555555u : 0xAAAAAAAAu;
+    int c = 0;
+    for (int w = w0; w < w1; ++w) {
+      const uint32_t v = ~(row[w] ^ __funnelshift_r(row[w], row[w == W - 1 ? 0 : w + 1], 1) ^ P);
+      c += __popc(v);
+    }
+    int d2 = 2 * c - 32 * (w1 - w0), inc = d2;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int nb = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+      if (lane >= o) inc += nb;
+    }
+    long long a = colh[y] + (inc - d2);
+    for (int w = w0; w < w1; ++w) {
+      const uint32_t v = ~(row[w] ^ __funnelshift_r(row[w], row[w == W - 1 ? 0 : w + 1], 1) ^ P);
+      for (int b = 0; b < 32; ++b) {
+        const __int128 h = a;
+        s[0] += h;
+        s[1] += h * h;
+        s[2] += h * h * h;
+        s[3] += h * h * h * h;
+        a += 2 * (long long)((v >> b) & 1u) - 1;
+      }
+    }
+  }
+  // reduce: warp shuffles of 64-bit halves are awkward for int128; go via smem
+#pragma unroll
+  for (int n = 0; n < 4; ++n) {
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long lo = (unsigned long long)s[n];
+      const long long hi = (long long)(s[n] >> 64);
+      const unsigned long long olo = __shfl_down_sync(0xFFFFFFFFu, lo, o);
+      const long long ohi = __shfl_down_sync(0xFFFFFFFFu, hi, o);
+      s[n] += (__int128)(((unsigned __int128)(unsigned long long)ohi << 64) | olo);
+    }
+    if (lane == 0) red[n][warp] = s[n];
+  }
+  __syncthreads();
+  if (tid < 4) {
+    __int128 tot = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) tot += red[tid][i];
+    slots[slot].sum[2 * tid] = (unsigned long long)tot;
+    slots[slot].sum[2 * tid + 1] = (unsigned long long)(tot >> 64);
+  }
+}
+
+cudaError_t launch_batch_sweeps(uint32_t *arena, SlotDesc *slots, const WorkTable *work,
+                                unsigned int *head, int grid, int threads, size_t smem_bytes,
+                                cudaStream_t st) {
+  // the dynamic shared-memory limit was raised by batch_occupancy() before
+  cudaError_t e = cudaMemsetAsync(head, 0, sizeof(unsigned int), st);
+  if (e != cudaSuccess) return e;
+  batch_sweep_kernel<<<grid, threads, smem_bytes, st>>>(arena, slots, work, head,
+                                                       (uint32_t)(smem_bytes / 4));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_moments(const uint32_t *arena, SlotDesc *slots, const WorkTable *work,
+                                 int nitems, int64_t max_L, cudaStream_t st) {
+  if (nitems <= 0) return cudaSuccess;
+  const size_t smem = (size_t)max_L * sizeof(long long);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute((const void *)batch_moments_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  batch_moments_kernel<<<nitems, 256, smem, st>>>(arena, slots, work);
+  return cudaGetLastError();
+}
+
+int batch_occupancy(int threads, size_t smem_bytes) {
+  int per_sm = 0;
+  // one limit for every batch: the largest staging buffer a tiling may ask for
+  cudaFuncSetAttribute((const void *)batch_sweep_kernel,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)batch_sweep_kernel,
+                                                    threads, smem_bytes) != cudaSuccess)
+    return 0;
+  return per_sm;
+}
+
+}  // namespace okz

@@ -1,0 +1,227 @@
+"""Continuous batching of simulation requests on one GPU (host loop only).
+
+A request asks for one lattice (L, p, q, seed) run for `budget` sweeps from the
+striped start, and gets back its exact sums and W^2 (Sec. I, Eq. (4)). The
+loop admits arrived requests whenever a slot and device memory are free, so
+requests that arrive while others run join at the next tick:
+
+* L <= 2048: a slot of an okz_batch pool (the arena is the HBM budget for
+  small lattices); every tick advances all active slots by up to
+  `tick_sweeps` sweeps in one graph-captured persistent launch;
+* L >= 4096: a simulation of its own (parity-plane stream kernel) on its own
+  CUDA stream, advanced by chunks of `tick_sweeps` sweeps; admitted while its
+  okz_device_bytes fit in the large-lattice budget and a stream is free.
+
+Both kinds run concurrently on the device. Every request evolves exactly as it
+would alone (same counter-based random stream), which tests check.
+All arithmetic runs in the CUDA library; this module only schedules.
+"""
+import dataclasses
+import time
+from collections import deque
+
+import numpy as np
+
+import paper_1110_6745_gb300 as okz
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    arrival: float  # seconds after the start of the session
+    L: int
+    p: float
+    q: float
+    seed: int
+    budget: int
+
+
+@dataclasses.dataclass
+class Result:
+    rid: int
+    Sk: list        # exact sums of (h - H0)^n, n = 1..4
+    H0: int
+    W2: float
+    admitted: float
+    finished: float
+    latency: float  # finished - arrival
+
+
+def poisson_requests(n=10000, rate=200.0, seed=2027, log_budget=(2.0, 4.0), exponents=(7, 13)):
+    """The served workload: Poisson arrivals at `rate`/s, L = 2^e with
+    e ~ U{exponents}, p ~ U{1.0, 0.75, 0.5}, q = 1 - p, budget =
+    round(10^U(log_budget)) sweeps, numpy PCG64 seeded."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    gaps = rng.exponential(1.0 / rate, size=n)
+    arrivals = np.cumsum(gaps) - gaps[0]
+    e = rng.integers(exponents[0], exponents[1] + 1, size=n)
+    p = rng.choice(np.array([1.0, 0.75, 0.5]), size=n)
+    budgets = np.round(10.0 ** rng.uniform(log_budget[0], log_budget[1], size=n)).astype(np.int64)
+    return [Request(i, float(arrivals[i]), int(1 << e[i]), float(p[i]), float(1.0 - p[i]),
+                    5000 + i, int(max(1, budgets[i]))) for i in range(n)]
+
+
+class Server:
+    def __init__(self, small_arena_bytes=1 << 31, max_slots=1024, large_bytes=8 << 30,
+                 max_large=16, tick_sweeps=128, large_threshold=4096):
+        import torch
+        self._torch = torch
+        self.pool = okz.Batch(arena_bytes=small_arena_bytes, max_slots=max_slots)
+        self.max_slots = max_slots
+        self.tick_sweeps = int(tick_sweeps)
+        self.large_threshold = int(large_threshold)
+        self.large_bytes = int(large_bytes)
+        self.large_used = 0
+        self.max_large = int(max_large)
+        self.streams = [torch.cuda.Stream() for _ in range(self.max_large)]
+        self.free_streams = list(range(self.max_large))
+        self.queue = deque()
+        self.small = {}   # slot -> [request, remaining, admitted]
+        self.large = {}   # rid -> [request, sim, stream index, remaining, event, admitted, nbytes]
+        self.results = {}
+        self.attempts = 0.0
+
+    # -- admission ----------------------------------------------------------
+    def _admit(self, now):
+        blocked = deque()
+        while self.queue:
+            r = self.queue.popleft()
+            if r.L >= self.large_threshold:
+                nbytes = okz.okz_device_bytes(r.L)
+                if self.free_streams and self.large_used + nbytes <= self.large_bytes:
+                    si = self.free_streams.pop()
+                    st = self.streams[si]
+                    sim = okz.Simulation(r.L, r.p, r.q, seed=r.seed,
+                                         kernel=okz.OKZ_KERNEL_PARITY_STREAM,
+                                         stream=st.cuda_stream)
+                    self.large_used += nbytes
+                    self.large[r.rid] = [r, sim, si, r.budget, None, now, nbytes]
+                    continue
+            else:
+                try:
+                    slot = self.pool.add(r.L, r.p, r.q, r.seed)
+                    self.small[slot] = [r, r.budget, now]
+                    continue
+                except okz.OkzError as e:
+                    if e.status != okz.OKZ_EBUSY:
+                        raise
+            blocked.append(r)  # no room yet: keep arrival order
+        self.queue = blocked
+
+    # -- one tick -------------------------------------------------------------
+    def _tick(self, t0):
+        torch = self._torch
+        # large lattices: enqueue the next chunk on their own streams
+        for rid, ent in self.large.items():
+            r, sim, si, remaining, ev, _, _ = ent
+            if remaining > 0 and (ev is None or ev.query()):
+                n = min(remaining, self.tick_sweeps)
+                sim.sweep(n)
+                ent[3] = remaining - n
+                ev = torch.cuda.Event()
+                ev.record(self.streams[si])
+                ent[4] = ev
+                self.attempts += float(r.L) ** 2 * n
+        # small lattices: one batched launch
+        sweeps = np.zeros(self.max_slots, np.int64)
+        for slot, ent in self.small.items():
+            n = min(ent[1], self.tick_sweeps)
+            sweeps[slot] = n
+            ent[1] -= n
+            self.attempts += float(ent[0].L) ** 2 * n
+        if sweeps.any():
+            self.pool.run(sweeps)
+            self.pool.sync()
+        now = time.perf_counter() - t0
+        # retire finished small slots: their exact sums in one launch
+        done = [slot for slot, ent in self.small.items() if ent[1] == 0]
+        for slot, (Sk, H0, _) in zip(done, self.pool.measure(done)):
+            r, _, adm = self.small.pop(slot)
+            N = r.L * r.L
+            W2 = float(N * Sk[1] - Sk[0] * Sk[0]) / (float(N) * float(N))
+            self.pool.remove(slot)
+            self.results[r.rid] = Result(r.rid, Sk, H0, W2, adm, now, now - r.arrival)
+        # retire finished large lattices
+        for rid in [rid for rid, ent in self.large.items()
+                    if ent[3] == 0 and (ent[4] is None or ent[4].query())]:
+            r, sim, si, _, _, adm, nbytes = self.large.pop(rid)
+            Sk, W2, _, _ = sim.moments()
+            H0 = sim.info().H0
+            sim.close()
+            self.large_used -= nbytes
+            self.free_streams.append(si)
+            fin = time.perf_counter() - t0
+            self.results[rid] = Result(rid, Sk, H0, W2, adm, fin, fin - r.arrival)
+        return bool(sweeps.any())
+
+    def run(self, requests):
+        """Serve `requests` (sorted by arrival) in real time; returns results by id."""
+        pending = deque(sorted(requests, key=lambda r: r.arrival))
+        t0 = time.perf_counter()
+        while pending or self.queue or self.small or self.large:
+            now = time.perf_counter() - t0
+            while pending and pending[0].arrival <= now:
+                self.queue.append(pending.popleft())
+            self._admit(now)
+            if not self.small and not self.large:
+                if pending:  # idle until the next arrival
+                    time.sleep(max(0.0, min(0.002, pending[0].arrival - now)))
+                continue
+            if not self._tick(t0):
+                time.sleep(0.0002)  # only large lattices in flight: poll gently
+        self.makespan = time.perf_counter() - t0
+        return self.results
+
+    def close(self):
+        for ent in self.large.values():
+            ent[1].close()
+        self.pool.close()
+
+
+def run_alone(r):
+    """The reference for one request: its lattice on its own."""
+    kernel = (okz.OKZ_KERNEL_PARITY_STREAM if r.L >= 4096 else okz.OKZ_KERNEL_PARITY_PLAIN)
+    with okz.Simulation(r.L, r.p, r.q, seed=r.seed, kernel=kernel) as sim:
+        sim.sweep(r.budget)
+        Sk, W2, _, _ = sim.moments()
+        return Sk, sim.info().H0, W2
+
+
+def bench(args, world, rank, local, unit):
+    """bench.py --workload served: 10^4 Poisson requests at 200/s."""
+    import json
+
+    import torch
+    torch.cuda.set_device(local)
+    reqs = poisson_requests()
+    srv = Server()
+    res = srv.run(reqs)
+    lat = np.array([res[r.rid].latency for r in reqs])
+    attempts = sum(float(r.L) ** 2 * r.budget for r in reqs)
+    value = attempts / srv.makespan / 1e9
+    # per-request runs on their own, one after another, on a sample
+    sample = reqs[:: max(1, len(reqs) // 200)]
+    t0 = time.perf_counter()
+    for r in sample:
+        run_alone(r)
+    alone_s = time.perf_counter() - t0
+    alone = sum(float(r.L) ** 2 * r.budget for r in sample) / alone_s / 1e9
+    srv.close()
+    if rank != 0:
+        return
+    line = {
+        "metric": "aggregate site-update attempts/s, served requests", "value": value,
+        "unit": unit, "n_gpus": world, "steps": 1, "warmup": 0,
+        "ms_per_step": srv.makespan * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic", "impl": "okz-serve",
+        "config": {"workload": "10^4 requests, Poisson 200/s (PCG64 2027), L = 2^e, "
+                               "e ~ U{7..13}, p ~ U{1, 0.75, 0.5}, q = 1 - p, budgets "
+                               "round(10^U(2,4)) sweeps, admitted by slot and HBM footprint",
+                   "requests": len(reqs), "tick_sweeps": srv.tick_sweeps},
+        "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                      "max": float(lat.max())},
+        "makespan_s": srv.makespan,
+        "per_request_alone": {"value": alone, "unit": unit, "sample": len(sample)},
+        "served_over_alone": value / alone,
+    }
+    print(json.dumps(line), flush=True)
