@@ -58,6 +58,56 @@ __device__ __forceinline__ u32x4 group_bits(uint64_t g, uint32_t t, uint32_t m,
                   (uint32_t)(seed >> 32));
 }
 
+// Philox4x32-10 round keys of one seed: k[2r] = seed_lo + r*W_A,
+// k[2r+1] = seed_hi + r*W_B (r = 0..9). Passed to kernels by value, so the
+// rounds read them as constant-bank operands instead of recomputing them.
+struct RoundKeys {
+  uint32_t k[20];
+};
+
+inline RoundKeys round_keys(uint64_t seed) {
+  RoundKeys rk;
+  uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    rk.k[2 * r] = k0;
+    rk.k[2 * r + 1] = k1;
+    k0 += kPhiloxWeylA;
+    k1 += kPhiloxWeylB;
+  }
+  return rk;
+}
+
+// Philox4x32-10 of counter (c0, c1, c2, c3) with precomputed round keys.
+__device__ __forceinline__ u32x4 philox10_rk(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                             const RoundKeys &rk) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t pa = (uint64_t)kPhiloxMulA * c0;
+    const uint64_t pb = (uint64_t)kPhiloxMulB * c2;
+    const uint32_t n0 = (uint32_t)(pb >> 32) ^ c1 ^ rk.k[2 * r];
+    const uint32_t n2 = (uint32_t)(pa >> 32) ^ c3 ^ rk.k[2 * r + 1];
+    c1 = (uint32_t)pb;
+    c3 = (uint32_t)pa;
+    c0 = n0;
+    c2 = n2;
+  }
+  u32x4 out;
+  out.v[0] = c0;
+  out.v[1] = c1;
+  out.v[2] = c2;
+  out.v[3] = c3;
+  return out;
+}
+
+// Three-input bitwise function with an explicit truth table (lop3.b32):
+// bit i of the result is bit ((a_i << 2) | (b_i << 1) | c_i) of LUT.
+template <uint32_t LUT>
+__device__ __forceinline__ uint32_t lop3(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t d;
+  asm("lop3.b32 %0, %1, %2, %3, %4;" : "=r"(d) : "r"(a), "r"(b), "r"(c), "n"(LUT));
+  return d;
+}
+
 // Acceptance thresholds of a simulation: accept a minimum iff U < P and a
 // maximum iff U < Q, U a k-bit uniform read most significant level first.
 struct Accept {

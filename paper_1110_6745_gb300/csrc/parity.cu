@@ -242,24 +242,35 @@ struct PModes {
   uint32_t p1, p2, q1, q2;  // k <= 1: all-ones masks for "bit must be 0" and "always"
 };
 
-template <int WPT, int MODE>
+// Flips of WPT words of one stage of half-sweep parity SP. The neighbour
+// tests use 3-input logic: for SP = 0 a minimum has all four neighbours equal
+// to its own bit ("both equal" table 0x81 on (l, r, c) and on (d, u, c)),
+// for SP = 1 all four differ (table 0x42); maxima are the reverse.
+template <int WPT, int MODE, int SP>
 __device__ __forceinline__ void pstage(const uint32_t c[WPT], uint32_t lbit, uint32_t rbit,
-                                       const uint32_t d[WPT], const uint32_t u[WPT], uint32_t S,
-                                       uint32_t a, const uint32_t r0[WPT], uint32_t g0,
-                                       uint32_t t, uint64_t seed, const Accept &acc,
+                                       const uint32_t d[WPT], const uint32_t u[WPT], uint32_t a,
+                                       const uint32_t r0[WPT], uint32_t g0, uint32_t t,
+                                       const RoundKeys &rk, const Accept &acc,
                                        const PModes &md, uint32_t f[WPT], uint32_t *mn0) {
+  constexpr uint32_t kMin = SP ? 0x42u : 0x81u;
+  constexpr uint32_t kMax = SP ? 0x81u : 0x42u;
   uint32_t mn[WPT], mx[WPT];
 #pragma unroll
   for (int j = 0; j < WPT; ++j) {
-    const uint32_t l = (c[j] << 1) | (j == 0 ? lbit : (c[j - 1] >> 31));
-    const uint32_t r = (c[j] >> 1) | ((j == WPT - 1 ? rbit : (c[j + 1] & 1u)) << 31);
-    parity_extrema(c[j] ^ S, l, r, d[j], u[j], a, mn[j], mx[j]);
+    const uint32_t l = __funnelshift_l(j == 0 ? (lbit << 31) : c[j - 1], c[j], 1);
+    const uint32_t r = __funnelshift_r(c[j], j == WPT - 1 ? rbit : c[j + 1], 1);
+    if (MODE == kPModeHalf) {
+      const uint32_t ar = a & ~r0[j];  // active and selected by the level-0 bit
+      f[j] = lop3<0x80>(lop3<kMin>(l, r, c[j]), lop3<kMin>(d[j], u[j], c[j]), ar);
+      if (j == 0) *mn0 = lop3<0x80>(lop3<kMin>(l, r, c[j]), lop3<kMin>(d[j], u[j], c[j]), a);
+    } else {
+      mn[j] = lop3<0x80>(lop3<kMin>(l, r, c[j]), lop3<kMin>(d[j], u[j], c[j]), a);
+      mx[j] = lop3<0x80>(lop3<kMax>(l, r, c[j]), lop3<kMax>(d[j], u[j], c[j]), a);
+    }
   }
+  if (MODE == kPModeHalf) return;
   *mn0 = mn[0];
-  if (MODE == kPModeHalf) {
-#pragma unroll
-    for (int j = 0; j < WPT; ++j) f[j] = mn[j] & ~r0[j];
-  } else if (MODE == kPModeK1) {
+  if (MODE == kPModeK1) {
 #pragma unroll
     for (int j = 0; j < WPT; ++j)
       f[j] = (mn[j] & ((~r0[j] & md.p1) | md.p2)) | (mx[j] & ((~r0[j] & md.q1) | md.q2));
@@ -283,7 +294,7 @@ __device__ __forceinline__ void pstage(const uint32_t c[WPT], uint32_t lbit, uin
       } else {
 #pragma unroll
         for (int gq = 0; gq < WPT / 4; ++gq) {
-          const u32x4 b = group_bits((uint64_t)(g0 + gq), t, (uint32_t)m, seed);
+          const u32x4 b = philox10_rk(g0 + gq, 0u, t, (uint32_t)m, rk);
 #pragma unroll
           for (int j = 0; j < 4; ++j) rr[4 * gq + j] = b.v[j];
         }
@@ -308,7 +319,7 @@ __device__ __forceinline__ void pstage(const uint32_t c[WPT], uint32_t lbit, uin
 template <int WPT, int F, int MODE>
 __global__ void __launch_bounds__(WPT == 4 ? 1024 : 512, 1)
 parity_stream_kernel(const uint32_t *__restrict__ src, uint32_t *__restrict__ dst, int L,
-                     int stages, uint32_t t0, uint64_t seed, Accept acc, PModes md,
+                     int stages, uint32_t t0, const RoundKeys rk, Accept acc, PModes md,
                      Ctrl *__restrict__ ctrl) {
   constexpr int NST = 2 * F;
   constexpr int NC = NST > 1 ? NST - 1 : 1;  // stages whose output is carried
@@ -375,6 +386,13 @@ parity_stream_kernel(const uint32_t *__restrict__ src, uint32_t *__restrict__ ds
   int y = yb - 2 * F;  // wrapped row of stream position i
   if (y < 0) y += L;
   const int r_origin = yb - 2 * F;
+  // every stage of a step shares one active mask: stage h works on row
+  // y-1-h in half-sweep h%2, and (y - 1 - h + h%2) has the parity of y - 1
+  uint32_t am = ((y - 1) & 1) ? 0xAAAAAAAAu : 0x55555555u;
+  // first group of this thread in row y-1 (stage 0); stage h: - h rows
+  int q0 = (y == 0) ? L - 1 : y - 1;
+  uint32_t gq0 = (uint32_t)q0 * groups_per_row + (uint32_t)(NG * tid);
+  const uint32_t wrap_groups = (uint32_t)L * groups_per_row;
 
   for (int i = 0; i < nin; ++i) {
     const bool ok = tma::mbar_wait(&full[slot], phase);
@@ -400,15 +418,14 @@ parity_stream_kernel(const uint32_t *__restrict__ src, uint32_t *__restrict__ ds
       uint32_t Rn[F][WPT];
 #pragma unroll
       for (int h = 0; h < NST; ++h) {
-        int q = y - 1 - h;
-        if (q < 0) q += L;
         const int s = h & 1;
         const uint32_t t = t0 + (uint32_t)(h >> 1);
-        const uint32_t g0 = (uint32_t)q * groups_per_row + (uint32_t)(NG * tid);
-        if (s == 0) {  // fresh level-0 words of row q, sweep t
+        uint32_t g0 = gq0 - (uint32_t)h * groups_per_row;  // row y-1-h, wrapped
+        if (q0 < h) g0 += wrap_groups;
+        if (s == 0) {  // fresh level-0 words of row y-1-h, sweep t
 #pragma unroll
           for (int gq = 0; gq < NG; ++gq) {
-            const u32x4 b = group_bits((uint64_t)(g0 + gq), t, 0u, seed);
+            const u32x4 b = philox10_rk(g0 + gq, 0u, t, 0u, rk);
 #pragma unroll
             for (int j = 0; j < 4; ++j) Rn[h >> 1][4 * gq + j] = b.v[j];
           }
@@ -420,8 +437,12 @@ parity_stream_kernel(const uint32_t *__restrict__ src, uint32_t *__restrict__ ds
         const uint32_t rbit = (h == 0) ? rb : WR[h > 0 ? h - 1 : 0];
         uint32_t f[WPT];
         // s = 1 uses the words of the same row drawn by stage h-1 last step
-        pstage<WPT, MODE>(c, lbit, rbit, d, u, s ? ~0u : 0u, active_mask(q, s),
-                          s == 0 ? Rn[h >> 1] : R[h >> 1], g0, t, seed, acc, md, f, &mn0[h]);
+        if (s == 0)
+          pstage<WPT, MODE, 0>(c, lbit, rbit, d, u, am, Rn[h >> 1], g0, t, rk, acc, md, f,
+                               &mn0[h]);
+        else
+          pstage<WPT, MODE, 1>(c, lbit, rbit, d, u, am, R[h >> 1], g0, t, rk, acc, md, f,
+                               &mn0[h]);
         fbit[h] = f[0] & 1u;
 #pragma unroll
         for (int j = 0; j < WPT; ++j) out[h][j] = c[j] ^ f[j];
@@ -504,6 +525,13 @@ parity_stream_kernel(const uint32_t *__restrict__ src, uint32_t *__restrict__ ds
     if (++sl1 == stages) sl1 = 0;
     if (++sl2 == stages) sl2 = 0;
     if (++y == L) y = 0;
+    am = ~am;
+    if (++q0 == L) {
+      q0 = 0;
+      gq0 = (uint32_t)(NG * tid);
+    } else {
+      gq0 += groups_per_row;
+    }
   }
 }
 
@@ -547,7 +575,7 @@ cudaError_t plaunch(const uint32_t *src, uint32_t *dst, int L, uint32_t t, uint6
     cached_L = L;
   }
   parity_stream_kernel<WPT, F, MODE><<<plan.grid, plan.threads, plan.smem, st>>>(
-      src, dst, L, plan.stages, t, seed, acc, md, ctrl);
+      src, dst, L, plan.stages, t, round_keys(seed), acc, md, ctrl);
   return cudaGetLastError();
 }
 
