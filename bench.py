@@ -48,8 +48,8 @@ N_SMS = 152
 # dram__bytes_read.sum + dram__bytes_write.sum of one sweep-kernel launch (ncu,
 # L = 65536, 2 sweeps per launch), per site; valid only for the kernel source
 # with this SHA-256 (traffic is reported as null once the source changes).
-TRAFFIC_BYTES_PER_SITE = {"parity": 1046466560 / 65536 ** 2}
-TRAFFIC_SOURCE_SHA = {"parity": "4cfe1f0cbbbd477d488b342b8850e8bdd3662fd1e09e5863e5a27a24588c0752"}
+TRAFFIC_BYTES_PER_SITE = {"parity": (556870144 + 489893376) / 65536 ** 2}
+TRAFFIC_SOURCE_SHA = {"parity": "7f35d7429097d45ac0a1bef97cb8320a9de4e0088da9bf5999553a3571834f33"}
 KERNEL_SOURCE = {"parity": "parity.cu", "slope": "sweep_stream.cu"}
 
 
