@@ -148,6 +148,23 @@ okz_status okz_create_ex(const okz_params *prm, void *dev_buf, size_t bytes,
  * (t + n > 2^32 - 1; nothing is enqueued), ECUDA (launch failure). */
 okz_status okz_sweep(okz_sim *sim, int64_t n);
 
+/* Enqueues n sweeps of the domain-decomposed random-sequential dynamics, the
+ * paper's own GPU update (Sec. II: blocks with dead borders, the origin moved
+ * at random every MCS, random attempts inside each block), as a statistical
+ * counterpart of the checkerboard sweep. Sweep t: offsets (ox, oy) = (r0, r1)
+ * mod 32 of Philox(counter (0, 0, t, 768)); 32 x 32 cells with origins
+ * (ox + 32i, oy + 32j) mod L, ids c = j*(L/32) + i; cell c receives 1024
+ * attempts, attempt a using words (r0, r1) (a even) or (r2, r3) (a odd) of
+ * Philox(counter (c, a/2, t, 1024)): local x = first & 31, local y =
+ * (first >> 16) & 31, u = second. Attempts on a cell's dead first column or
+ * first row do nothing (two dead edges, as in Fig. 1 of the paper);
+ * elsewhere a minimum moves iff u < round(p 2^32), a maximum iff
+ * u < round(q 2^32) (round half to even; no selection factor). Needs a
+ * parity-plane simulation (EUNSUPPORTED otherwise) and L % 32 == 0; shares t
+ * with okz_sweep. Errors: EINVAL (n < 0), EUNSUPPORTED, EOVERFLOW (t + n >
+ * 2^32 - 1), ECUDA (launch failure). */
+okz_status okz_sweep_rs(okz_sim *sim, int64_t n);
+
 /* Synchronizing. Reconstructs the heights from the slopes (Sec. I, Eq. (3),
  * anchored at H0 = h(0,0)) and returns the exact sums S1 = sum h,
  * S2 = sum h^2 and the squared width of Sec. I, Eq. (4),
@@ -171,6 +188,26 @@ okz_status okz_moments(okz_sim *sim, okz_i128 Sk[4], double *W2, double *skew,
  * |h| >= 2^31; out is then undefined), ECUDA. */
 okz_status okz_heights(okz_sim *sim, int64_t y0, int64_t ny, int32_t *out,
                        int out_is_device);
+
+/* Synchronizing. Interface profiles for the power spectrum of Sec. III
+ * (Eqs. (15)-(16)): col[x] = sum_y (h(x,y) - H0) and row[y] = sum_x
+ * (h(x,y) - H0), x, y = 0 .. L-1, exact int64, into caller-owned host arrays
+ * of L values (either may be NULL). Allocates 4 L ceil(L/R) + 28 L bytes
+ * (plus 40 L for okz_psd) of stream-ordered device scratch for the call, R
+ * being the rows per counting band (16 .. 2048; 2048 at L = 131072, i.e.
+ * 35 MiB). Errors: EINVAL, ENOMEM, ECUDA. */
+okz_status okz_profiles(okz_sim *sim, int64_t *col, int64_t *row);
+
+/* Synchronizing. The power spectrum of Sec. III, Eqs. (15)-(16), on the two
+ * k axes, averaged over the x and y directions:
+ *   S[k] = (|h(k,0)|^2 + |h(0,k)|^2) / 2,  k = 0 .. L-1 (wave number 2 pi k / L),
+ *   h(k,0) = (1/L) sum_{x,y} (h(x,y) - <h>) e^{-2 pi i k x / L},
+ * (the d = 2 normalisation L^{-d/2}; S[0] = 0 as the mean is removed; the
+ * sign of the exponent does not change |h(k)|). Computed from the exact
+ * profiles (okz_profiles) by radix-2 FFTs in fp64 on the device. S is a
+ * caller-owned host array of L doubles. Needs a power-of-two L (EUNSUPPORTED
+ * otherwise). Errors: EINVAL, EUNSUPPORTED, ENOMEM, ECUDA. */
+okz_status okz_psd(okz_sim *sim, double *S);
 
 /* Synchronizing. Copies the state buffer (X plane then Y plane, layout
  * above) to planes_out (device memory if out_is_device, else host) and

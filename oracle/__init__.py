@@ -71,6 +71,9 @@ def lib():
     L.orc_width2.restype = c.c_double
     L.orc_skew_kurt.argtypes = [c.c_int64, i64p, c.c_int64, f64p]
     L.orc_skew_kurt.restype = None
+    L.orc_ddrs_sweeps.argtypes = [c.c_int64, c.c_int64, u8p, u8p, c.POINTER(c.c_int64),
+                                  c.c_uint64, c.c_uint64, c.c_int64, c.c_uint64, c.c_uint64]
+    L.orc_ddrs_sweeps.restype = c.c_int
     L.orc_window_init_flat.argtypes = [c.c_int64, c.c_int64, c.c_int64, c.c_int64, u8p,
                                        u8p]
     L.orc_window_init_flat.restype = None
@@ -208,6 +211,17 @@ class Sim:
         H0 = ctypes.c_int64(self.H0)
         lib().orc_rs_sweeps(self.L, self.X, self.Y, ctypes.byref(H0), self.seed,
                             self.t, int(n), rs_threshold(self.p), rs_threshold(self.q))
+        self.H0 = H0.value
+        self.t += int(n)
+
+    def ddrs_sweep(self, n=1, C=32):
+        """Domain-decomposed random-sequential sweeps (cells C x C, dead borders,
+        random offsets; p, q used directly)."""
+        H0 = ctypes.c_int64(self.H0)
+        if lib().orc_ddrs_sweeps(self.L, C, self.X, self.Y, ctypes.byref(H0), self.seed,
+                                 self.t, int(n), rs_threshold(self.p),
+                                 rs_threshold(self.q)) != 0:
+            raise ValueError("C must be a power of two >= 4 dividing L")
         self.H0 = H0.value
         self.t += int(n)
 

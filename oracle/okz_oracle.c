@@ -352,6 +352,76 @@ ORC_API void orc_rs_sweeps(int64_t L, uint8_t *X, uint8_t *Y, int64_t *H0,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Domain-decomposed random-sequential dynamics (Sec. II: blocks with dead   */
+/* borders, the origin moved at random every MCS, random update attempts     */
+/* inside each block). Sweep t:                                               */
+/*  - offsets (ox, oy) = (r0 mod C, r1 mod C) of Philox(ctr = (0, 0, t, 768)); */
+/*  - cell (i, j), i, j < L/C, has origin ((ox + iC) mod L, (oy + jC) mod L)  */
+/*    and id c = j*(L/C) + i;                                                 */
+/*  - it receives C*C attempts a = 0, 1, ... in order; attempt a uses words   */
+/*    (r0, r1) (a even) or (r2, r3) (a odd) of Philox(ctr = (c, a/2, t,       */
+/*    1024)): local x = first & (C-1), local y = (first >> 16) & (C-1),       */
+/*    u = second. Attempts on the cell's dead border (local x = 0 or local   */
+/*    y = 0) do nothing; elsewhere a minimum moves iff u < P32, a maximum iff */
+/*    u < Q32 (32-bit thresholds, no selection factor).                       */
+/* Two dead edges suffice, as in the paper's Fig. 1: a site's move flips its */
+/* four bonds, and the only bonds a cell shares with its neighbours in x and  */
+/* y join its last column (row) to their dead first column (row). Cells thus  */
+/* share no bond that anyone flips, and the cell order does not matter. C    */
+/* must be a power of two dividing L.                                         */
+/* ------------------------------------------------------------------------ */
+ORC_API int orc_ddrs_sweeps(int64_t L, int64_t C, uint8_t *X, uint8_t *Y, int64_t *H0,
+                            uint64_t seed, uint64_t t0, int64_t n, uint64_t P32,
+                            uint64_t Q32)
+{
+    if (C < 4 || (C & (C - 1)) != 0 || L % C != 0)
+        return -1;
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    int64_t ncell = L / C;
+    for (int64_t it = 0; it < n; ++it) {
+        uint64_t t = t0 + (uint64_t)it;
+        uint32_t octr[4] = {0, 0, (uint32_t)t, 768u}, o[4];
+        orc_philox4x32_10(octr, key, o);
+        int64_t ox = (int64_t)(o[0] & (uint32_t)(C - 1));
+        int64_t oy = (int64_t)(o[1] & (uint32_t)(C - 1));
+        for (int64_t cj = 0; cj < ncell; ++cj)
+            for (int64_t ci = 0; ci < ncell; ++ci) {
+                uint64_t c = (uint64_t)(cj * ncell + ci);
+                int64_t x0 = (ox + ci * C) % L, y0 = (oy + cj * C) % L;
+                uint32_t r[4] = {0, 0, 0, 0};
+                for (int64_t a = 0; a < C * C; ++a) {
+                    if (a % 2 == 0) {
+                        uint32_t ctr[4] = {(uint32_t)c, (uint32_t)(a / 2), (uint32_t)t, 1024u};
+                        orc_philox4x32_10(ctr, key, r);
+                    }
+                    uint32_t first = (a % 2 == 0) ? r[0] : r[2];
+                    uint32_t u = (a % 2 == 0) ? r[1] : r[3];
+                    int64_t lx = (int64_t)(first & (uint32_t)(C - 1));
+                    int64_t ly = (int64_t)((first >> 16) & (uint32_t)(C - 1));
+                    if (lx == 0 || ly == 0)
+                        continue;
+                    int64_t x = (x0 + lx) % L, y = (y0 + ly) % L;
+                    int64_t xm = (x == 0) ? L - 1 : x - 1, ym = (y == 0) ? L - 1 : y - 1;
+                    uint8_t *left = &X[y * L + xm], *right = &X[y * L + x];
+                    uint8_t *down = &Y[ym * L + x], *up = &Y[y * L + x];
+                    int is_min = (*left == 0) && (*right == 1) && (*down == 0) && (*up == 1);
+                    int is_max = (*left == 1) && (*right == 0) && (*down == 1) && (*up == 0);
+                    int accept = (is_min && u < P32) || (is_max && u < Q32);
+                    if (!accept)
+                        continue;
+                    *left ^= 1;
+                    *right ^= 1;
+                    *down ^= 1;
+                    *up ^= 1;
+                    if (x == 0 && y == 0)
+                        *H0 += is_min ? 2 : -2;
+                }
+            }
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* A window of a larger periodic L x L lattice, for checking very large runs  */
 /* site by site. The window holds the bonds of the sites                     */
 /*   (x0 + i mod L, y0 + j mod L),  0 <= i < w, 0 <= j < h,                   */

@@ -62,11 +62,14 @@ _SIGS = {
     "okz_create_ex": (_c.c_int, [_c.POINTER(okz_params), _vp, _c.c_size_t, _vp,
                                  _c.POINTER(_vp)]),
     "okz_sweep": (_c.c_int, [_vp, _c.c_int64]),
+    "okz_sweep_rs": (_c.c_int, [_vp, _c.c_int64]),
     "okz_width2": (_c.c_int, [_vp, _c.POINTER(okz_i128), _c.POINTER(okz_i128),
                               _c.POINTER(_c.c_double)]),
     "okz_moments": (_c.c_int, [_vp, _c.POINTER(okz_i128), _c.POINTER(_c.c_double),
                                _c.POINTER(_c.c_double), _c.POINTER(_c.c_double)]),
     "okz_heights": (_c.c_int, [_vp, _c.c_int64, _c.c_int64, _vp, _c.c_int]),
+    "okz_profiles": (_c.c_int, [_vp, _vp, _vp]),
+    "okz_psd": (_c.c_int, [_vp, _vp]),
     "okz_state": (_c.c_int, [_vp, _vp, _c.c_int, _c.POINTER(_c.c_int64),
                              _c.POINTER(_c.c_uint64)]),
     "okz_restore": (_c.c_int, [_vp, _vp, _c.c_int, _c.c_int64, _c.c_uint64]),
@@ -170,6 +173,10 @@ def okz_sweep(h, n):
     _check(lib().okz_sweep(h, int(n)), "okz_sweep")
 
 
+def okz_sweep_rs(h, n):
+    _check(lib().okz_sweep_rs(h, int(n)), "okz_sweep_rs")
+
+
 def okz_width2(h):
     """-> (S1, S2, W2) with S1 = sum h and S2 = sum h^2 as Python ints."""
     S1, S2, W2 = okz_i128(), okz_i128(), ctypes.c_double()
@@ -201,6 +208,21 @@ def okz_heights(h, y0, ny, L, out=None):
         ptr, is_dev = out.data_ptr(), 1
     _check(lib().okz_heights(h, int(y0), int(ny), ptr, is_dev), "okz_heights")
     return out
+
+
+def okz_profiles(h, L):
+    """-> (col, row): int64 numpy arrays of the column and row sums of h - H0."""
+    col = np.empty(int(L), np.int64)
+    row = np.empty(int(L), np.int64)
+    _check(lib().okz_profiles(h, col.ctypes.data, row.ctypes.data), "okz_profiles")
+    return col, row
+
+
+def okz_psd(h, L):
+    """-> S: float64 numpy array of the axis-averaged power spectrum, k = 0..L-1."""
+    S = np.empty(int(L), np.float64)
+    _check(lib().okz_psd(h, S.ctypes.data), "okz_psd")
+    return S
 
 
 def okz_state(h, L, out=None):
@@ -283,6 +305,9 @@ class Simulation:
     def sweep(self, n=1):
         okz_sweep(self.h, n)
 
+    def sweep_rs(self, n=1):
+        okz_sweep_rs(self.h, n)
+
     def width2(self):
         return okz_width2(self.h)
 
@@ -291,6 +316,12 @@ class Simulation:
 
     def heights(self, y0=0, ny=None, out=None):
         return okz_heights(self.h, y0, self.L - y0 if ny is None else ny, self.L, out)
+
+    def profiles(self):
+        return okz_profiles(self.h, self.L)
+
+    def psd(self):
+        return okz_psd(self.h, self.L)
 
     def state(self, out=None):
         return okz_state(self.h, self.L, out)

@@ -1,0 +1,117 @@
+"""Steady-state statistics across replicas (Kelling & Odor, Secs. III and IV).
+
+* The distribution of the squared width W^2 in the steady state: its
+  cumulants kappa_1..kappa_4, written through the raw moments
+  nu_n = <(W^2)^n> (Sec. IV, the cumulant-moment relations), and the scaled
+  distribution Psi_L(x) = <W^2> P_L(W^2 / <W^2>) (Sec. IV).
+* The effective roughness exponent alpha_eff(L) (Sec. III, Eq. (13)) and the
+  finite-size-scaling fit alpha_eff(L) = alpha + a1 w1 L^(-w1) (Eq. (14),
+  correction exponent read with a minus sign so that it vanishes as L grows).
+* The power spectrum S(k) on the axes (Sec. III, Eqs. (15)-(16)) averaged
+  over replicas and sampling times.
+
+Samples come from batched replicas (okz_batch_*): every replica is run to the
+steady state and then sampled every `every` sweeps; each W^2 sample is exact
+(Eq. (4)), each spectrum is computed on the device (okz_psd).
+"""
+import numpy as np
+
+import paper_1110_6745_gb300 as okz
+
+
+def w2_cumulants(samples):
+    """kappa_1..kappa_4 of the samples from their raw moments nu_n:
+    kappa_1 = nu_1, kappa_2 = nu_2 - nu_1^2,
+    kappa_3 = nu_3 - 3 nu_1 nu_2 + 2 nu_1^3,
+    kappa_4 = nu_4 - 4 nu_3 nu_1 - 3 nu_2^2 + 12 nu_1^2 nu_2 - 6 nu_1^4,
+    evaluated in extended precision."""
+    x = np.asarray(samples, dtype=np.longdouble).ravel()
+    nu = [np.mean(x ** n) for n in range(1, 5)]
+    n1, n2, n3, n4 = nu
+    k1 = n1
+    k2 = n2 - n1 * n1
+    k3 = n3 - 3 * n1 * n2 + 2 * n1 ** 3
+    k4 = n4 - 4 * n3 * n1 - 3 * n2 * n2 + 12 * n1 * n1 * n2 - 6 * n1 ** 4
+    return [float(k) for k in (k1, k2, k3, k4)]
+
+
+def psi(samples, bins=50):
+    """Psi_L(x) = <W^2> P_L(W^2 / <W^2>): a normalised histogram of
+    x = W^2 / <W^2>. Returns (bin centres, density)."""
+    w = np.asarray(samples, dtype=np.float64).ravel()
+    x = w / w.mean()
+    dens, edges = np.histogram(x, bins=bins, density=True)
+    return 0.5 * (edges[1:] + edges[:-1]), dens
+
+
+def steady_state_w2(L, replicas, burnin, nsamples, every, p=1.0, q=0.0, seed0=0):
+    """W^2 samples (replicas x nsamples) of `replicas` independent lattices of
+    size L (seeds seed0 + r), each run `burnin` sweeps from the striped start
+    and then sampled every `every` sweeps."""
+    with okz.Batch([L] * replicas, [p] * replicas, [q] * replicas,
+                   [seed0 + r for r in range(replicas)]) as b:
+        _advance(b, replicas, burnin)
+        out = np.empty((replicas, nsamples))
+        for k in range(nsamples):
+            _advance(b, replicas, every)
+            W2, _, _ = b.stats()
+            out[:, k] = W2
+    return out
+
+
+def _advance(b, replicas, sweeps, per_launch=1 << 16):
+    """All replicas of batch b forward by `sweeps`, at most `per_launch` sweeps
+    per batched launch (keeps single launches short)."""
+    while sweeps > 0:
+        n = min(sweeps, per_launch)
+        b.run([n] * replicas)
+        sweeps -= n
+
+
+def alpha_eff(Ls, w2_means):
+    """alpha_eff(L) = [ln W(L) - ln W(L/2)] / ln 2 (Eq. (13)) with W = sqrt(<W^2>),
+    for every L in Ls whose half is also in Ls. Returns (L values, alpha_eff)."""
+    w = dict(zip((int(l) for l in Ls), (float(v) for v in w2_means)))
+    out_L, out_a = [], []
+    for L in sorted(w):
+        if L // 2 in w and L % 2 == 0:
+            out_L.append(L)
+            out_a.append(0.5 * (np.log(w[L]) - np.log(w[L // 2])) / np.log(2.0))
+    return np.array(out_L), np.array(out_a)
+
+
+def fit_alpha(Ls, a_eff, omega):
+    """Least-squares fit of alpha_eff(L) = alpha + c L^(-omega) (Eq. (14),
+    c = a1 omega) at a fixed correction exponent omega. Returns (alpha, c)."""
+    Ls = np.asarray(Ls, dtype=np.float64)
+    A = np.stack([np.ones_like(Ls), Ls ** (-float(omega))], axis=1)
+    (alpha, c), *_ = np.linalg.lstsq(A, np.asarray(a_eff, dtype=np.float64), rcond=None)
+    return float(alpha), float(c)
+
+
+def steady_state_psd(L, replicas, burnin, nsamples, every, p=1.0, q=0.0, seed0=0):
+    """The axis spectrum S[k] (okz_psd) averaged over `replicas` lattices of
+    size L (seeds seed0 + r) and `nsamples` times `every` sweeps apart after
+    `burnin` sweeps. The replicas run batched; each sample's state is moved
+    into one simulation (okz_restore) whose spectrum is taken on the device."""
+    acc = np.zeros(int(L))
+    with okz.Batch([L] * replicas, [p] * replicas, [q] * replicas,
+                   [seed0 + r for r in range(replicas)]) as b, \
+            okz.Simulation(L, p, q, seed=seed0, kernel=okz.OKZ_KERNEL_PARITY_PLAIN) as sim:
+        _advance(b, replicas, burnin)
+        for _ in range(nsamples):
+            _advance(b, replicas, every)
+            for r in range(replicas):
+                planes, H0, t = b.state(r)
+                sim.restore(planes, H0, t)
+                acc += sim.psd()
+    return acc / (replicas * nsamples)
+
+
+def spectrum_slope(S, kmin, kmax):
+    """Least-squares slope of ln S[k] against ln k over kmin <= k <= kmax
+    (indices, k standing for 2 pi k / L); S ~ k^(-2-2 alpha) in the steady
+    state (Sec. III)."""
+    k = np.arange(len(S))
+    m = (k >= kmin) & (k <= kmax)
+    return float(np.polyfit(np.log(k[m]), np.log(np.asarray(S)[m]), 1)[0])

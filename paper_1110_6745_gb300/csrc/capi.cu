@@ -170,10 +170,17 @@ okz_status okz_create_ex(const okz_params *prm, void *dev_buf, size_t bytes, voi
   }
   int wpt = prm->words_per_thread, fuse = prm->sweeps_per_pass;
   if (streamed) {
-    // defaults measured on GB300: 8 words per thread where the row allows it;
-    // the parity plane fuses two sweeps per pass on large lattices
-    if (wpt == 0) wpt = stream_wpt_valid(prm->L, 8) ? 8 : 4;
-    if (fuse == 0) fuse = (kernel == OKZ_KERNEL_PARITY_STREAM && prm->L >= 65536) ? 2 : 1;
+    // defaults measured on GB300. Slope planes: 8 words per thread where the
+    // row allows it, one sweep per pass. Parity plane: two sweeps per pass at
+    // every size, 8 words per thread from L = 16384 up (4 below: a CTA spans
+    // one short row, and 4 words per thread doubles its threads).
+    if (kernel == OKZ_KERNEL_PARITY_STREAM) {
+      if (wpt == 0) wpt = (prm->L >= 16384 && stream_wpt_valid(prm->L, 8)) ? 8 : 4;
+      if (fuse == 0) fuse = 2;
+    } else {
+      if (wpt == 0) wpt = stream_wpt_valid(prm->L, 8) ? 8 : 4;
+      if (fuse == 0) fuse = 1;
+    }
     if (!stream_wpt_valid(prm->L, wpt) || (fuse != 1 && fuse != 2)) {
       set_error("words_per_thread must be 4 or 8 (8 needs L % 8192 == 0) and "
                 "sweeps_per_pass 1 or 2");
@@ -316,6 +323,39 @@ okz_status okz_sweep(okz_sim *sim, int64_t n) {
   return OKZ_OK;
 }
 
+okz_status okz_sweep_rs(okz_sim *sim, int64_t n) {
+  if (!sim || n < 0) {
+    set_error("null simulation or negative sweep count");
+    return OKZ_EINVAL;
+  }
+  if (!sim->parity) {
+    set_error("okz_sweep_rs needs a parity-plane simulation (kernel PARITY_PLAIN or "
+              "PARITY_STREAM)");
+    return OKZ_EUNSUPPORTED;
+  }
+  if (sim->prm.L % 32 != 0) {
+    set_error("okz_sweep_rs needs L % 32 == 0");
+    return OKZ_EUNSUPPORTED;
+  }
+  if ((uint64_t)n > 0xFFFFFFFFull - sim->t) {
+    set_error("sweep counter would pass 2^32 - 1");
+    return OKZ_EOVERFLOW;
+  }
+  // 32-bit thresholds, round half to even, no selection factor
+  const int mode = std::fegetround();
+  std::fesetround(FE_TONEAREST);
+  const uint64_t P32 = (uint64_t)std::nearbyint(std::ldexp(sim->prm.p, 32));
+  const uint64_t Q32 = (uint64_t)std::nearbyint(std::ldexp(sim->prm.q, 32));
+  std::fesetround(mode);
+  for (int64_t i = 0; i < n; ++i) {
+    cudaError_t e = launch_ddrs(sim->planes[sim->cur], sim->prm.L, (uint32_t)sim->t,
+                                sim->prm.seed, P32, Q32, sim->ctrl, sim->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "random-sequential sweep launch");
+    sim->t += 1;
+  }
+  return OKZ_OK;
+}
+
 static okz_status sync_and_check(okz_sim *sim) {
   cudaError_t e = cudaStreamSynchronize(sim->stream);
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
@@ -446,6 +486,61 @@ okz_status okz_heights(okz_sim *sim, int64_t y0, int64_t ny, int32_t *out,
     return OKZ_EOVERFLOW;
   }
   return OKZ_OK;
+}
+
+// Profiles (and optionally the axis power spectrum) into host arrays.
+static okz_status profiles_and_psd(okz_sim *sim, int64_t *col, int64_t *row, double *S) {
+  const int64_t L = sim->prm.L;
+  const bool fft = S != nullptr;
+  const size_t scratch = psd_scratch_bytes(L, fft);
+  const size_t vec = ((size_t)L * sizeof(int64_t) + 255) & ~(size_t)255;
+  const size_t bytes = scratch + 3 * vec;
+  char *buf = nullptr;
+  cudaError_t e = cudaMallocAsync((void **)&buf, bytes, sim->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error("device scratch allocation for the profiles failed");
+    return OKZ_ENOMEM;
+  }
+  int64_t *dcol = reinterpret_cast<int64_t *>(buf + scratch);
+  int64_t *drow = reinterpret_cast<int64_t *>(buf + scratch + vec);
+  double *dS = reinterpret_cast<double *>(buf + scratch + 2 * vec);
+  e = launch_profiles(sim->planes[sim->cur], L, sim->parity, sim->hcol, buf, dcol, drow,
+                      sim->stream);
+  if (e == cudaSuccess && fft) e = launch_psd(dcol, drow, L, buf, dS, sim->stream);
+  if (e == cudaSuccess && col)
+    e = cudaMemcpyAsync(col, dcol, (size_t)L * sizeof(int64_t), cudaMemcpyDeviceToHost,
+                        sim->stream);
+  if (e == cudaSuccess && row)
+    e = cudaMemcpyAsync(row, drow, (size_t)L * sizeof(int64_t), cudaMemcpyDeviceToHost,
+                        sim->stream);
+  if (e == cudaSuccess && fft)
+    e = cudaMemcpyAsync(S, dS, (size_t)L * sizeof(double), cudaMemcpyDeviceToHost,
+                        sim->stream);
+  cudaFreeAsync(buf, sim->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "profiles");
+  return sync_and_check(sim);
+}
+
+okz_status okz_profiles(okz_sim *sim, int64_t *col, int64_t *row) {
+  if (!sim) {
+    set_error("null simulation");
+    return OKZ_EINVAL;
+  }
+  return profiles_and_psd(sim, col, row, nullptr);
+}
+
+okz_status okz_psd(okz_sim *sim, double *S) {
+  if (!sim || !S) {
+    set_error("null simulation or output");
+    return OKZ_EINVAL;
+  }
+  const int64_t L = sim->prm.L;
+  if ((L & (L - 1)) != 0) {
+    set_error("okz_psd needs a power-of-two L");
+    return OKZ_EUNSUPPORTED;
+  }
+  return profiles_and_psd(sim, nullptr, nullptr, S);
 }
 
 okz_status okz_state(okz_sim *sim, uint32_t *planes_out, int out_is_device, int64_t *H0,

@@ -10,6 +10,7 @@
 // Power sums S_n = sum (h - H0)^n are exact: 64-bit per word and per thread,
 // 128-bit per thread total, then per block, then a single-block final sum.
 #include "okz_internal.h"
+#include "okz_planes.cuh"
 
 namespace okz {
 
@@ -39,26 +40,6 @@ __device__ __forceinline__ long long warp_exclusive_scan64(long long v, int lane
 
 // hcol[y] = h(0,y) - H0 = sum_{y'<y} sigma_y(0,y'): one block, each thread a
 // contiguous run of rows, block-wide exclusive scan of the run totals.
-// sigma_y(0,y) as a bit: read from the Y plane, or (parity plane B) from
-// b(0,y) ^ b(0,y+1) ^ p(0,y) == 0.
-template <bool PAR>
-__device__ __forceinline__ uint32_t col0_up(const uint32_t *__restrict__ P, int64_t L,
-                                            int64_t W, int64_t y) {
-  if (!PAR) return P[L * W + y * W] & 1u;
-  const int64_t yu = (y == L - 1) ? 0 : y + 1;
-  return ~(P[y * W] ^ P[yu * W] ^ (uint32_t)(y & 1)) & 1u;
-}
-
-// X-plane word w of row y: stored, or (parity plane) ~(b ^ b(x+1) ^ p).
-template <bool PAR>
-__device__ __forceinline__ uint32_t x_word(const uint32_t *__restrict__ row, int64_t W,
-                                           int64_t w, int64_t y) {
-  if (!PAR) return row[w];
-  const uint32_t c = row[w], n = row[w == W - 1 ? 0 : w + 1];
-  const uint32_t P = (y & 1) ? 0x55555555u : 0xAAAAAAAAu;  // sites with x + y odd
-  return ~(c ^ __funnelshift_r(c, n, 1) ^ P);
-}
-
 template <bool PAR>
 __global__ void __launch_bounds__(1024)
 colscan_kernel(const uint32_t *__restrict__ planes, int64_t L, int64_t *__restrict__ hcol) {
@@ -199,6 +180,15 @@ partials_sum_kernel(const unsigned long long *__restrict__ partials, int nblocks
     ctrl->sum[2 * tid] = (unsigned long long)tot;
     ctrl->sum[2 * tid + 1] = (unsigned long long)(tot >> 64);
   }
+}
+
+cudaError_t launch_colscan(const uint32_t *planes, int64_t L, bool parity, int64_t *hcol,
+                           cudaStream_t st) {
+  if (parity)
+    colscan_kernel<true><<<1, 1024, 0, st>>>(planes, L, hcol);
+  else
+    colscan_kernel<false><<<1, 1024, 0, st>>>(planes, L, hcol);
+  return cudaGetLastError();
 }
 
 static int reduce_blocks(int64_t L) {

@@ -42,6 +42,9 @@ cudaError_t launch_sweep_stream(const uint32_t *src, uint32_t *dst, int64_t L,
 cudaError_t launch_power_sums(const uint32_t *planes, int64_t L, bool parity, int nmom,
                               int64_t *hcol, unsigned long long *partials,
                               Ctrl *ctrl, cudaStream_t st);
+// hcol[y] = h(0,y) - H0 (the column-0 scan of the height reconstruction).
+cudaError_t launch_colscan(const uint32_t *planes, int64_t L, bool parity, int64_t *hcol,
+                           cudaStream_t st);
 cudaError_t launch_heights(const uint32_t *planes, int64_t L, bool parity, int64_t y0,
                            int64_t ny, int64_t *hcol, int32_t *out, Ctrl *ctrl,
                            cudaStream_t st);
@@ -53,7 +56,18 @@ cudaError_t launch_parity_stream(const uint32_t *src, uint32_t *dst, int64_t L, 
                                  uint64_t seed, const Accept &acc, int wpt, int fuse,
                                  Ctrl *ctrl, cudaStream_t st);
 cudaError_t launch_to_slopes(const uint32_t *B, int64_t L, uint32_t *out, cudaStream_t st);
+cudaError_t launch_ddrs(uint32_t *B, int64_t L, uint32_t t, uint64_t seed, uint64_t P32,
+                        uint64_t Q32, Ctrl *ctrl, cudaStream_t st);
 cudaError_t launch_from_slopes(const uint32_t *slopes, int64_t L, long long H0, int64_t *bcol,
                                uint32_t *B, cudaStream_t st);
+
+// Interface profiles and power spectrum (psd.cu). Scratch for L: see
+// psd_scratch_bytes; col, row (L int64 each) are device arrays.
+size_t psd_scratch_bytes(int64_t L, bool fft);
+cudaError_t launch_profiles(const uint32_t *planes, int64_t L, bool parity, int64_t *hcol,
+                            void *scratch, int64_t *col, int64_t *row, cudaStream_t st);
+// S[k], k = 0..L-1 (device array) from col and row; L a power of two.
+cudaError_t launch_psd(const int64_t *col, const int64_t *row, int64_t L, void *scratch,
+                       double *S, cudaStream_t st);
 
 }  // namespace okz

@@ -1,0 +1,95 @@
+"""W^2 cumulants and Psi_L(x) (Sec. IV) and the steady-state sampler."""
+import numpy as np
+import pytest
+
+
+def test_cumulants_two_point_closed_form():
+    """Values a and b with equal weight: kappa_1 = (a+b)/2, kappa_2 = s^2,
+    kappa_3 = 0, kappa_4 = -2 s^4 with s = (b-a)/2."""
+    from paper_1110_6745_gb300.analysis import w2_cumulants
+    a, b = 3.0, 7.0
+    k = w2_cumulants([a, b] * 500)
+    s = (b - a) / 2
+    assert k[0] == pytest.approx((a + b) / 2, rel=1e-15)
+    assert k[1] == pytest.approx(s ** 2, rel=1e-14)
+    assert abs(k[2]) < 1e-12
+    assert k[3] == pytest.approx(-2 * s ** 4, rel=1e-12)
+
+
+def test_cumulants_match_central_moments():
+    """Against the central-moment route: kappa_2 = mu_2, kappa_3 = mu_3,
+    kappa_4 = mu_4 - 3 mu_2^2 (scipy.stats.moment)."""
+    from scipy import stats
+    from paper_1110_6745_gb300.analysis import w2_cumulants
+    x = np.random.default_rng(5).gamma(3.0, 2.0, size=20000)
+    k = w2_cumulants(x)
+    m2, m3, m4 = (stats.moment(x, n) for n in (2, 3, 4))
+    assert k[0] == pytest.approx(x.mean(), rel=1e-12)
+    assert k[1] == pytest.approx(m2, rel=1e-10)
+    assert k[2] == pytest.approx(m3, rel=1e-9)
+    assert k[3] == pytest.approx(m4 - 3 * m2 ** 2, rel=1e-8)
+
+
+def test_psi_is_a_normalised_density_with_unit_mean():
+    from paper_1110_6745_gb300.analysis import psi
+    x = np.random.default_rng(1).lognormal(0.0, 0.3, size=50000)
+    c, d = psi(x, bins=80)
+    width = c[1] - c[0]
+    assert np.sum(d) * width == pytest.approx(1.0, rel=1e-12)
+    assert np.sum(c * d) * width == pytest.approx(1.0, abs=0.01)
+
+
+def test_alpha_eff_of_a_pure_power_law():
+    """W^2 = a^2 L^(2 alpha) gives alpha_eff(L) = alpha at every L (Eq. (13))."""
+    from paper_1110_6745_gb300.analysis import alpha_eff
+    Ls = [64, 128, 256, 512, 1000]
+    Le, a = alpha_eff(Ls, [3.0 * L ** 0.78 for L in Ls])
+    assert Le.tolist() == [128, 256, 512]  # 1000 has no half in the list
+    assert np.allclose(a, 0.39, rtol=0, atol=1e-14)
+
+
+def test_alpha_eff_with_a_correction_term():
+    """W = a L^alpha (1 + b L^(-w)): alpha_eff = alpha + log2 of the ratio of
+    the correction factors, by hand."""
+    from paper_1110_6745_gb300.analysis import alpha_eff
+    al, b, w = 0.393, -0.9, 1.16
+    Ls = [2 ** e for e in range(5, 12)]
+    W = [2.0 * L ** al * (1 + b * L ** -w) for L in Ls]
+    Le, a = alpha_eff(Ls, [x * x for x in W])
+    want = [al + np.log2((1 + b * L ** -w) / (1 + b * (L / 2) ** -w)) for L in Le]
+    assert np.allclose(a, want, rtol=0, atol=1e-13)
+
+
+def test_fit_alpha_recovers_the_parameters():
+    from paper_1110_6745_gb300.analysis import fit_alpha
+    Ls = np.array([256, 512, 1024, 2048, 4096, 8192], float)
+    a = 0.393 - 1.44 * Ls ** -1.16
+    alpha, c = fit_alpha(Ls, a, 1.16)
+    assert alpha == pytest.approx(0.393, abs=1e-12)
+    assert c == pytest.approx(-1.44, abs=1e-9)
+
+
+def test_spectrum_slope_of_a_power_law():
+    from paper_1110_6745_gb300.analysis import spectrum_slope
+    k = np.arange(1, 513, dtype=float)
+    S = np.concatenate([[0.0], 5.0 * k ** -2.786])
+    assert spectrum_slope(S, 2, 100) == pytest.approx(-2.786, abs=1e-12)
+
+
+@pytest.mark.gpu
+def test_steady_state_sampler_matches_single_runs():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_1110_6745_gb300 as okz
+    from paper_1110_6745_gb300 import _build
+    from paper_1110_6745_gb300.analysis import steady_state_w2, w2_cumulants
+    _build.build()
+    w = steady_state_w2(64, replicas=6, burnin=300, nsamples=5, every=40, seed0=70)
+    for r in range(6):
+        with okz.Simulation(64, 1.0, 0.0, seed=70 + r, kernel=okz.OKZ_KERNEL_PARITY_PLAIN) as s:
+            s.sweep(300)
+            for k in range(5):
+                s.sweep(40)
+                assert s.width2()[2] == w[r, k]
+    k = w2_cumulants(w)
+    assert k[0] > 0.25 and k[1] > 0

@@ -376,3 +376,55 @@ def test_growth_series_L16384_golden(okz):
             assert (sim.info().t, sim.info().H0, s1, s2, w2) == (t, H0, S1, S2, W2)
         planes, _, _ = sim.state()
         assert hashlib.sha256(planes.tobytes()).hexdigest() == digest
+
+
+# --------------------------------------------------------------------------
+# Domain-decomposed random-sequential sweeps (okz_sweep_rs)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("L,p,q,seed", [(32, 1.0, 0.0, 1), (64, 0.75, 0.25, 2),
+                                         (128, 1.0, 1.0, 3), (96, 0.5, 0.5, 4)])
+def test_random_sequential_sweeps_match_oracle(okz, orc, L, p, q, seed):
+    ref = orc.Sim(L, p, q, seed)
+    with okz.Simulation(L, p, q, seed=seed, kernel=okz.OKZ_KERNEL_PARITY_PLAIN) as sim:
+        for n in (1, 4):
+            ref.ddrs_sweep(n)
+            sim.sweep_rs(n)
+            _compare(sim, ref)
+        # interleaved with checkerboard sweeps, sharing the sweep counter
+        ref.sweep(2)
+        sim.sweep(2)
+        ref.ddrs_sweep(1)
+        sim.sweep_rs(1)
+        _compare(sim, ref)
+        S1, S2, W2 = sim.width2()
+        assert (S1, S2) == ref.sums() and W2 == ref.width2()
+
+
+def test_random_sequential_needs_parity_plane(okz):
+    with okz.Simulation(64, 1.0, 0.0, seed=1, kernel=okz.OKZ_KERNEL_PLAIN) as sim:
+        with pytest.raises(okz.OkzError) as e:
+            sim.sweep_rs(1)
+        assert e.value.status == okz.OKZ_EUNSUPPORTED
+
+
+def test_random_sequential_growth_exponent(okz):
+    """The paper's own (random-sequential, blocked) dynamics and the
+    checkerboard schedule give compatible growth exponents at L = 2048."""
+    def beta(step_rs):
+        ts = [0] + [int(round(10 ** (1 + 2 * j / 19))) for j in range(20)]
+        acc = np.zeros(len(ts))
+        for sd in range(3):
+            with okz.Simulation(2048, 1.0, 0.0, seed=40 + sd) as sim:
+                w, done = [], 0
+                for t in ts:
+                    (sim.sweep_rs if step_rs else sim.sweep)(t - done)
+                    done = t
+                    w.append(sim.width2()[2])
+            acc += np.array(w)
+        acc /= 3
+        tt, ww = np.array(ts[1:], float), acc[1:]
+        m = tt >= 100
+        return np.polyfit(np.log(tt[m]), 0.5 * np.log(ww[m] - 0.25), 1)[0]
+    b_rs, b_cb = beta(True), beta(False)
+    assert 0.20 <= b_rs <= 0.28 and 0.20 <= b_cb <= 0.28, (b_rs, b_cb)
+    assert abs(b_rs - b_cb) < 0.04, (b_rs, b_cb)

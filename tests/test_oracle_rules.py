@@ -253,3 +253,61 @@ def test_random_sequential_variant(orc):
     sim = orc.Sim(32, 0.5, 0.5, 8)
     sim.rs_sweep(20)
     _check_invariants(sim)
+
+
+def test_domain_decomposed_random_sequential(orc):
+    """The blocked random-sequential dynamics keeps every height-function
+    invariant; every move changes a height by 2, and with p = 1, q = 0 the
+    surface only rises."""
+    sim = orc.Sim(64, 1.0, 0.0, 12)
+    for _ in range(6):
+        before, _ = sim.sums()
+        sim.ddrs_sweep(1)
+        _check_invariants(sim)
+        after, _ = sim.sums()
+        assert after > before and (after - before) % 2 == 0
+    sim = orc.Sim(96, 0.5, 0.5, 13)
+    sim.ddrs_sweep(10)
+    _check_invariants(sim)
+    with pytest.raises(ValueError):
+        orc.Sim(96, 1.0, 0.0, 1).ddrs_sweep(1, C=64)  # 64 does not divide 96
+
+
+def _ddrs_by_hand(orc, h, L, C, p, q, seed, t, cell_order):
+    """One blocked random-sequential sweep on a height array, written from
+    the definition: random origin, C x C cells, C*C attempts per cell from
+    the cell's own Philox stream, first column and first row dead."""
+    P32, Q32 = orc.rs_threshold(p), orc.rs_threshold(q)
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    o = orc.philox4x32_10([0, 0, t, 768], key)
+    ox, oy = int(o[0]) % C, int(o[1]) % C
+    n = L // C
+    for c in cell_order:
+        x0, y0 = (ox + (c % n) * C) % L, (oy + (c // n) * C) % L
+        for a in range(C * C):
+            r = orc.philox4x32_10([c, a // 2, t, 1024], key)
+            first, u = (int(r[0]), int(r[1])) if a % 2 == 0 else (int(r[2]), int(r[3]))
+            lx, ly = first % C, (first >> 16) % C
+            if lx == 0 or ly == 0:
+                continue
+            x, y = (x0 + lx) % L, (y0 + ly) % L
+            nb = [h[y, (x - 1) % L], h[y, (x + 1) % L], h[(y - 1) % L, x], h[(y + 1) % L, x]]
+            if all(v == h[y, x] + 1 for v in nb) and u < P32:
+                h[y, x] += 2
+            elif all(v == h[y, x] - 1 for v in nb) and u < Q32:
+                h[y, x] -= 2
+    return h
+
+
+def test_domain_decomposed_cells_are_independent(orc):
+    """The oracle's blocked sweep equals the definition applied to heights by
+    hand, with the cells taken in reverse order (they share no flipped bond),
+    for one cell covering the lattice and for 2 x 2 cells."""
+    for L, C, seed in [(16, 16, 5), (32, 16, 6), (32, 8, 9)]:
+        sim = orc.Sim(L, 0.75, 0.25, seed)
+        h = orc.Sim(L, 0.75, 0.25, seed).heights()
+        for t in range(3):
+            sim.ddrs_sweep(1, C=C)
+            h = _ddrs_by_hand(orc, h, L, C, 0.75, 0.25, seed, t,
+                              reversed(range((L // C) ** 2)))
+            assert np.array_equal(sim.heights(), h), (L, C, t)
