@@ -9,12 +9,18 @@ requests that arrive while others run join at the next tick:
   small lattices); every tick advances all active slots by up to
   `tick_sweeps` sweeps in one graph-captured persistent launch;
 * L >= 4096: a simulation of its own (parity-plane stream kernel) on its own
-  CUDA stream, advanced by chunks of `tick_sweeps` sweeps; admitted while its
-  okz_device_bytes fit in the large-lattice budget and a stream is free.
+  CUDA stream, admitted while its okz_device_bytes fit in the large-lattice
+  budget and a stream is free. Its budget is enqueued in chunks of about
+  `chunk_attempts` site updates, at most `ahead` chunks in flight, each
+  closed by an event, so the stream never drains while the host loop runs
+  and the host never blocks on a full launch queue.
 
-Both kinds run concurrently on the device. Every request evolves exactly as it
-would alone (same counter-based random stream), which tests check.
-All arithmetic runs in the CUDA library; this module only schedules.
+The loop never waits on the device: the batched launch is also closed by an
+event and its slots are retired, and new small requests admitted, when that
+event has fired. Both kinds run concurrently on the device. Every request
+evolves exactly as it would alone (same counter-based random stream), which
+tests check. All arithmetic runs in the CUDA library; this module only
+schedules.
 """
 import dataclasses
 import time
@@ -63,26 +69,32 @@ def poisson_requests(n=10000, rate=200.0, seed=2027, log_budget=(2.0, 4.0), expo
 
 class Server:
     def __init__(self, small_arena_bytes=1 << 31, max_slots=1024, large_bytes=8 << 30,
-                 max_large=16, tick_sweeps=128, large_threshold=4096):
+                 max_large=16, tick_sweeps=128, large_threshold=4096, chunk_attempts=2e10,
+                 ahead=2, max_chunk_sweeps=256):
         import torch
         self._torch = torch
         self.pool = okz.Batch(arena_bytes=small_arena_bytes, max_slots=max_slots)
+        self.pool_stream = torch.cuda.ExternalStream(self.pool.stream)
+        self.small_event = None
         self.max_slots = max_slots
         self.tick_sweeps = int(tick_sweeps)
         self.large_threshold = int(large_threshold)
         self.large_bytes = int(large_bytes)
         self.large_used = 0
         self.max_large = int(max_large)
+        self.chunk_attempts = float(chunk_attempts)
+        self.ahead = int(ahead)
+        self.max_chunk_sweeps = int(max_chunk_sweeps)
         self.streams = [torch.cuda.Stream() for _ in range(self.max_large)]
         self.free_streams = list(range(self.max_large))
         self.queue = deque()
         self.small = {}   # slot -> [request, remaining, admitted]
-        self.large = {}   # rid -> [request, sim, stream index, remaining, event, admitted, nbytes]
+        self.large = {}   # rid -> _Large
         self.results = {}
         self.attempts = 0.0
 
     # -- admission ----------------------------------------------------------
-    def _admit(self, now):
+    def _admit(self, now, small_ok):
         blocked = deque()
         while self.queue:
             r = self.queue.popleft()
@@ -90,14 +102,22 @@ class Server:
                 nbytes = okz.okz_device_bytes(r.L)
                 if self.free_streams and self.large_used + nbytes <= self.large_bytes:
                     si = self.free_streams.pop()
-                    st = self.streams[si]
-                    sim = okz.Simulation(r.L, r.p, r.q, seed=r.seed,
-                                         kernel=okz.OKZ_KERNEL_PARITY_STREAM,
-                                         stream=st.cuda_stream)
+                    # device memory from torch's caching allocator, tied to the
+                    # request's stream: creating and closing a simulation then
+                    # never calls cudaMalloc / cudaFree, which would stall the
+                    # other streams
+                    with self._torch.cuda.stream(self.streams[si]):
+                        sim = okz.Simulation(r.L, r.p, r.q, seed=r.seed,
+                                             kernel=okz.OKZ_KERNEL_PARITY_STREAM,
+                                             torch_buffer=True,
+                                             stream=self.streams[si].cuda_stream)
                     self.large_used += nbytes
-                    self.large[r.rid] = [r, sim, si, r.budget, None, now, nbytes]
+                    chunk = int(min(self.max_chunk_sweeps,
+                                    max(1, round(self.chunk_attempts / (r.L * r.L)))))
+                    self.large[r.rid] = _Large(r, sim, si, r.budget, deque(), now, nbytes,
+                                               chunk)
                     continue
-            else:
+            elif small_ok:
                 try:
                     slot = self.pool.add(r.L, r.p, r.q, r.seed)
                     self.small[slot] = [r, r.budget, now]
@@ -105,35 +125,44 @@ class Server:
                 except okz.OkzError as e:
                     if e.status != okz.OKZ_EBUSY:
                         raise
-            blocked.append(r)  # no room yet: keep arrival order
+            blocked.append(r)  # no room yet (or the pool is busy): keep arrival order
         self.queue = blocked
 
-    # -- one tick -------------------------------------------------------------
-    def _tick(self, t0):
+    # -- large lattices: keep `ahead` chunks in flight ------------------------
+    def _pump_large(self):
         torch = self._torch
-        # large lattices: enqueue the next chunk on their own streams
-        for rid, ent in self.large.items():
-            r, sim, si, remaining, ev, _, _ = ent
-            if remaining > 0 and (ev is None or ev.query()):
-                n = min(remaining, self.tick_sweeps)
-                sim.sweep(n)
-                ent[3] = remaining - n
+        moved = False
+        for ent in self.large.values():
+            while ent.inflight and ent.inflight[0].query():
+                ent.inflight.popleft()
+                moved = True
+            while ent.remaining > 0 and len(ent.inflight) < self.ahead:
+                n = min(ent.remaining, ent.chunk)
+                ent.sim.sweep(n)
+                ent.remaining -= n
                 ev = torch.cuda.Event()
-                ev.record(self.streams[si])
-                ent[4] = ev
-                self.attempts += float(r.L) ** 2 * n
-        # small lattices: one batched launch
-        sweeps = np.zeros(self.max_slots, np.int64)
-        for slot, ent in self.small.items():
-            n = min(ent[1], self.tick_sweeps)
-            sweeps[slot] = n
-            ent[1] -= n
-            self.attempts += float(ent[0].L) ** 2 * n
-        if sweeps.any():
-            self.pool.run(sweeps)
-            self.pool.sync()
+                ev.record(self.streams[ent.si])
+                ent.inflight.append(ev)
+                self.attempts += float(ent.r.L) ** 2 * n
+                moved = True
+        return moved
+
+    def _retire_large(self, t0):
+        done = [rid for rid, ent in self.large.items() if ent.remaining == 0 and not ent.inflight]
+        for rid in done:
+            ent = self.large.pop(rid)
+            Sk, W2, _, _ = ent.sim.moments()
+            H0 = ent.sim.info().H0
+            ent.sim.close()
+            self.large_used -= ent.nbytes
+            self.free_streams.append(ent.si)
+            fin = time.perf_counter() - t0
+            self.results[rid] = Result(rid, Sk, H0, W2, ent.admitted, fin, fin - ent.r.arrival)
+        return bool(done)
+
+    # -- small lattices: one batched launch at a time -------------------------
+    def _retire_small(self, t0):
         now = time.perf_counter() - t0
-        # retire finished small slots: their exact sums in one launch
         done = [slot for slot, ent in self.small.items() if ent[1] == 0]
         for slot, (Sk, H0, _) in zip(done, self.pool.measure(done)):
             r, _, adm = self.small.pop(slot)
@@ -141,41 +170,65 @@ class Server:
             W2 = float(N * Sk[1] - Sk[0] * Sk[0]) / (float(N) * float(N))
             self.pool.remove(slot)
             self.results[r.rid] = Result(r.rid, Sk, H0, W2, adm, now, now - r.arrival)
-        # retire finished large lattices
-        for rid in [rid for rid, ent in self.large.items()
-                    if ent[3] == 0 and (ent[4] is None or ent[4].query())]:
-            r, sim, si, _, _, adm, nbytes = self.large.pop(rid)
-            Sk, W2, _, _ = sim.moments()
-            H0 = sim.info().H0
-            sim.close()
-            self.large_used -= nbytes
-            self.free_streams.append(si)
-            fin = time.perf_counter() - t0
-            self.results[rid] = Result(rid, Sk, H0, W2, adm, fin, fin - r.arrival)
-        return bool(sweeps.any())
+
+    def _launch_small(self):
+        sweeps = np.zeros(self.max_slots, np.int64)
+        for slot, ent in self.small.items():
+            n = min(ent[1], self.tick_sweeps)
+            sweeps[slot] = n
+            ent[1] -= n
+            self.attempts += float(ent[0].L) ** 2 * n
+        if not sweeps.any():
+            return False
+        self.pool.run(sweeps)
+        ev = self._torch.cuda.Event()
+        ev.record(self.pool_stream)
+        self.small_event = ev
+        return True
 
     def run(self, requests):
         """Serve `requests` (sorted by arrival) in real time; returns results by id."""
         pending = deque(sorted(requests, key=lambda r: r.arrival))
         t0 = time.perf_counter()
-        while pending or self.queue or self.small or self.large:
+        while pending or self.queue or self.small or self.large or self.small_event:
             now = time.perf_counter() - t0
             while pending and pending[0].arrival <= now:
                 self.queue.append(pending.popleft())
-            self._admit(now)
-            if not self.small and not self.large:
-                if pending:  # idle until the next arrival
+            busy = False
+            pool_idle = self.small_event is None or self.small_event.query()
+            if pool_idle and self.small_event is not None:
+                self.small_event = None
+                self._retire_small(t0)
+                busy = True
+            self._admit(now, small_ok=pool_idle)
+            if pool_idle:
+                busy |= self._launch_small()
+            busy |= self._pump_large()
+            busy |= self._retire_large(t0)
+            if not busy:
+                if not self.small and not self.large and pending and not self.queue:
                     time.sleep(max(0.0, min(0.002, pending[0].arrival - now)))
-                continue
-            if not self._tick(t0):
-                time.sleep(0.0002)  # only large lattices in flight: poll gently
+                else:
+                    time.sleep(0.00005)
         self.makespan = time.perf_counter() - t0
         return self.results
 
     def close(self):
         for ent in self.large.values():
-            ent[1].close()
+            ent.sim.close()
         self.pool.close()
+
+
+@dataclasses.dataclass
+class _Large:
+    r: Request
+    sim: object
+    si: int
+    remaining: int      # sweeps not yet enqueued
+    inflight: deque     # events closing the enqueued chunks
+    admitted: float
+    nbytes: int
+    chunk: int
 
 
 def run_alone(r):
@@ -220,6 +273,10 @@ def bench(args, world, rank, local, unit):
                    "requests": len(reqs), "tick_sweeps": srv.tick_sweeps},
         "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                       "max": float(lat.max())},
+        "latency_by_L_s": {str(L): [float(np.percentile(lat[m], 50)),
+                                    float(np.percentile(lat[m], 99))]
+                           for L in sorted(set(r.L for r in reqs))
+                           for m in [np.array([r.L == L for r in reqs])]},
         "makespan_s": srv.makespan,
         "per_request_alone": {"value": alone, "unit": unit, "sample": len(sample)},
         "served_over_alone": value / alone,

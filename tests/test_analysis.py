@@ -93,3 +93,61 @@ def test_steady_state_sampler_matches_single_runs():
                 assert s.width2()[2] == w[r, k]
     k = w2_cumulants(w)
     assert k[0] > 0.25 and k[1] > 0
+
+
+@pytest.fixture(scope="module")
+def steady():
+    """Steady-state W^2 samples at L = 128, 256, 512: 304 replicas each (two
+    per SM of the batched kernel), 4 L^1.61 sweeps of burn-in from the striped
+    start (saturation is reached near L^1.61 sweeps at s_sel = 1/2), then 8
+    samples L^1.61 sweeps apart (about one correlation time)."""
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1110_6745_gb300 import _build
+    _build.build()
+    from paper_1110_6745_gb300.analysis import steady_state_w2
+    out = {}
+    for L in (128, 256, 512):
+        tx = L ** 1.61
+        out[L] = steady_state_w2(L, 304, int(4 * tx), 8, int(tx), seed0=100000 + 1000 * L)
+    return out
+
+
+@pytest.mark.gpu
+def test_alpha_eff_near_the_paper_value(steady):
+    """alpha_eff(L) (Eq. (13)) at L = 256 and 512 within 0.05 of the paper's
+    alpha = 0.393(4) (Sec. III), approached from below; each estimate has a
+    sampling error of about 0.01 (a statistical pin, not parity)."""
+    from paper_1110_6745_gb300.analysis import alpha_eff
+    Ls = sorted(steady)
+    Le, a = alpha_eff(Ls, [steady[L].mean() for L in Ls])
+    assert Le.tolist() == [256, 512]
+    assert np.all((a > 0.33) & (a < 0.43)), a
+    assert 0.35 < a.mean() < 0.41, a
+
+
+@pytest.mark.gpu
+def test_cumulant_ratios_do_not_depend_on_L(steady):
+    """kappa_n ~ L^(2 n alpha) (Sec. IV) makes kappa_2 / kappa_1^2 the same at
+    every L; its sampling error here is a few per cent."""
+    from paper_1110_6745_gb300.analysis import w2_cumulants
+    r = [w2_cumulants(steady[L]) for L in sorted(steady)]
+    ratio = [k[1] / k[0] ** 2 for k in r]
+    assert max(ratio) / min(ratio) < 1.3, ratio
+    assert all(0.05 < x < 0.2 for x in ratio), ratio
+    assert all(k[2] > 0 for k in r)  # W^2 is skewed to large widths
+
+
+@pytest.mark.gpu
+def test_steady_state_spectrum_slope():
+    """S(k) ~ k^(-2-2 alpha) at small k in the steady state (Sec. III): the
+    slope over 2 pi k / L in [0.025, 0.2] at L = 256 within 0.15 of
+    -2 - 2 (0.393)."""
+    from paper_1110_6745_gb300.analysis import spectrum_slope, steady_state_psd
+    L = 256
+    tx = L ** 1.61
+    S = steady_state_psd(L, 152, int(4 * tx), 4, int(tx), seed0=7 * L)
+    assert S[0] == 0.0 and np.all(S[1:] > 0)
+    assert np.allclose(S[1:], S[1:][::-1], rtol=1e-9)  # real surface: S(k) = S(-k)
+    slope = spectrum_slope(S, 1, 8)
+    assert abs(slope - (-2 - 2 * 0.393)) < 0.15, slope
