@@ -117,7 +117,7 @@ class ClockSampler:
                     reasons.add(n)
         if not sm:
             return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "sm_min_mhz": min(sm),
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
@@ -278,6 +278,8 @@ def run_gpu(args, world, rank, local):
     host_planes.copy_(start_planes.cpu())
     torch.cuda.synchronize(dev)
     _barrier(world)
+    e2e_clocks = ClockSampler(local)
+    e2e_clocks.start()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         sim.restore(host_planes, 0, 0)
@@ -285,6 +287,7 @@ def run_gpu(args, world, rank, local):
         sim.width2()
     torch.cuda.synchronize(dev)
     e2e_s = _max_over_ranks(world, time.perf_counter() - t0, dev)
+    e2e_clk = e2e_clocks.stop()
     e2e_value = world * N * SWEEPS_PER_STEP * e2e_steps / e2e_s / 1e9
     h2d = L * L // 4 + 8            # both planes + H0
     d2h = 256 + 4                   # control block (sums, H0) + error word
@@ -318,7 +321,7 @@ def run_gpu(args, world, rank, local):
         "slope_roofline_frac": (N * fuse / per_launch_s) * 0.5 / (peak * 1e9),
         "gpu_launches": launches,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "steps": e2e_steps},
+                "d2h_bytes_per_step": d2h, "steps": e2e_steps, "clocks": e2e_clk},
         "w2_final": w2_final,
         "clocks": clk,
     }
@@ -414,6 +417,141 @@ def run_batched(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
+# Integer work of one attempt of the blocked random-sequential sweep (ALU
+# pipe): half a Philox4x32-10 block (10 three-input xors; its 10 wide
+# multiplies run on the FMA pipe), decoding the site (2), the dead-border test
+# (2), the five neighbour/own bits (3 shifts), the extremum tests (4 logic
+# ops), the acceptance compare (2), the flip and the touched-row mask (4).
+RS_ALU_OPS_PER_ATTEMPT = 10 + 2 + 2 + 3 + 4 + 2 + 4
+
+
+def run_rs(args, world, rank, local):
+    """--workload rs: the paper's own dynamics (blocked random-sequential
+    sweeps, okz_sweep_rs) on the L = 2^17 lattice; a step = 2 sweeps + exact W^2."""
+    import torch
+
+    import paper_1110_6745_gb300 as okz
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    L = args.L
+    N = L * L
+    per_step = 2
+    steps = min(args.steps, 8)
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        sim = okz.Simulation(L, 1.0, 0.0, seed=SEED + rank, torch_buffer=True,
+                             kernel=okz.OKZ_KERNEL_PARITY_PLAIN)
+    for _ in range(args.warmup):
+        sim.sweep_rs(per_step)
+        sim.width2()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    _barrier(world)
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    t0.record(stream)
+    for k in range(steps):
+        evs[k][0].record(stream)
+        sim.sweep_rs(per_step)
+        evs[k][1].record(stream)
+        sim.width2()
+    t1.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    _barrier(world)
+    ms = _max_over_ranks(world, t0.elapsed_time(t1), dev)
+    launch_s = sum(a.elapsed_time(b) for a, b in evs) / 1e3 / (steps * per_step)
+    value = world * N * per_step * steps / (ms / 1e3) / 1e9
+    sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
+    alu_peak = N_SMS * ALU_LANES_PER_SM * sm_mhz * 1e6 / 1e12
+    alu_ops = RS_ALU_OPS_PER_ATTEMPT * N
+    sim.close()
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": ms / steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "impl": "okz-rs",
+        "config": {"workload": "blocked random-sequential dynamics (32x32 cells, two dead "
+                               "edges, origin moved every sweep), L=2^17, striped start, "
+                               "p=1 q=0, seed=11; step = 2 sweeps + exact W^2",
+                   "L": L, "sweeps_per_step": per_step,
+                   "l2": "inputs larger than L2 (2 GiB parity plane)"},
+        "roofline": {"bound": "alu", "achieved": alu_ops / launch_s / 1e12, "peak": alu_peak,
+                     "unit": "Tops/s", "frac": alu_ops / launch_s / 1e12 / alu_peak,
+                     "traffic": None, "kernel": "ddrs_kernel",
+                     "peak_kind": "derived: 152 SMs x 64 INT32 lanes x sampled SM clock",
+                     "ops_per_launch": alu_ops, "launch_ms": launch_s * 1e3},
+        "gpu_launches": steps * (per_step + 3),
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_spectrum(args, world, rank, local):
+    """--workload spectrum: interface profiles and the axis power spectrum
+    (okz_psd) of the L = 2^17 lattice after 64 sweeps; a step = one spectrum."""
+    import torch
+
+    import paper_1110_6745_gb300 as okz
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    L = args.L
+    N = L * L
+    steps = min(args.steps, 16)
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        sim = okz.Simulation(L, 1.0, 0.0, seed=SEED + rank, torch_buffer=True)
+    sim.sweep(64)
+    for _ in range(args.warmup):
+        sim.psd()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    clocks = ClockSampler(local)
+    _barrier(world)
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    w0 = time.perf_counter()
+    for k in range(steps):
+        evs[k][0].record(stream)
+        S = sim.psd()
+        evs[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    wall = _max_over_ranks(world, time.perf_counter() - w0, dev)
+    clk = clocks.stop()
+    _barrier(world)
+    gpu_s = sum(a.elapsed_time(b) for a, b in evs) / 1e3 / steps
+    peak, peak_kind = _peaks()
+    alg = 0.125 * N  # the parity plane read once by the counting pass
+    sim.close()
+    if rank != 0:
+        return
+    line = {
+        "metric": "sites/s through profiles + axis spectrum", "value": world * N * steps / wall / 1e9,
+        "unit": "1e9 sites/s", "n_gpus": world, "steps": steps, "warmup": args.warmup,
+        "ms_per_step": wall / steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32/f64", "data": "synthetic", "impl": "okz-spectrum",
+        "config": {"workload": "okz_psd of the L=2^17 lattice after 64 growth sweeps "
+                               "(p=1 q=0 s_sel=1/2, seed=11); host-synchronous call, 3 x 1 MiB "
+                               "device-to-host copies included", "L": L,
+                   "l2": "inputs larger than L2 (2 GiB parity plane)"},
+        "roofline": {"bound": "hbm", "achieved": alg / gpu_s / 1e9, "peak": peak,
+                     "unit": "GB/s", "frac": alg / gpu_s / 1e9 / peak, "traffic": None,
+                     "kernel": "profile_count_kernel (+ scan and FFT, all in the interval)",
+                     "bytes_per_call": alg, "gpu_ms_per_call": gpu_s * 1e3,
+                     "peak_kind": peak_kind},
+        "S_k1": float(S[1]),
+        "gpu_launches": steps * (7 + int(L).bit_length() - 1),  # 4 profile + 3 + log2 L FFT kernels
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -425,7 +563,8 @@ def main():
     ap.add_argument("--kernel", default="auto", choices=sorted(KERNELS))
     ap.add_argument("--wpt", type=int, default=0, help="words per thread (0 = library choice)")
     ap.add_argument("--fuse", type=int, default=0, help="sweeps per launch (0 = library choice)")
-    ap.add_argument("--workload", default="growth", choices=["growth", "batched", "served"])
+    ap.add_argument("--workload", default="growth",
+                    choices=["growth", "batched", "served", "rs", "spectrum"])
     ap.add_argument("--budget-frac", type=int, default=64,
                     help="batched: run ceil(4 L^1.61)/frac sweeps per replica")
     ap.add_argument("--baseline-frac", type=int, default=2048,
@@ -439,6 +578,10 @@ def main():
     elif args.workload == "served":
         from paper_1110_6745_gb300 import serve
         serve.bench(args, world, rank, local, UNIT)
+    elif args.workload == "rs":
+        run_rs(args, world, rank, local)
+    elif args.workload == "spectrum":
+        run_spectrum(args, world, rank, local)
     else:
         run_gpu(args, world, rank, local)
     if world > 1:

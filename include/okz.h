@@ -139,7 +139,9 @@ okz_status okz_create(int64_t L, double p, double q, uint64_t seed, okz_sim **ou
  * aligned, which the caller keeps alive until okz_destroy; otherwise the
  * library allocates. stream is a cudaStream_t (NULL = the library creates
  * its own non-blocking stream); all work of this simulation is ordered on
- * it. Errors: EINVAL, EUNSUPPORTED, ENOMEM, ECUDA. */
+ * it. With a caller's stream the call returns once the initialisation (the
+ * striped start) is enqueued on that stream; with the library's own stream
+ * it waits for it. Errors: EINVAL, EUNSUPPORTED, ENOMEM, ECUDA. */
 okz_status okz_create_ex(const okz_params *prm, void *dev_buf, size_t bytes,
                          void *stream, okz_sim **out);
 
@@ -181,6 +183,17 @@ okz_status okz_width2(okz_sim *sim, okz_i128 *S1, okz_i128 *S2, double *W2);
  * Needs L <= 131072. Any output pointer may be NULL. */
 okz_status okz_moments(okz_sim *sim, okz_i128 Sk[4], double *W2, double *skew,
                        double *kurt);
+
+/* okz_moments in two halves, for callers that must not block while other
+ * streams work: okz_moments_enqueue launches the power-sum kernels on the
+ * simulation's stream and returns at once; okz_moments_fetch waits for that
+ * stream (record an event after enqueue and poll it to know when the wait is
+ * free) and returns what okz_moments would have. Sweeps enqueued in between
+ * do not change the result of the enqueued sums; a later measurement call
+ * overwrites them. Errors: as okz_moments. */
+okz_status okz_moments_enqueue(okz_sim *sim);
+okz_status okz_moments_fetch(okz_sim *sim, okz_i128 Sk[4], double *W2, double *skew,
+                             double *kurt);
 
 /* Synchronizing. Writes h(x, y) for rows y0 .. y0+ny-1 (Sec. I, Eq. (3)) as
  * int32, row-major, ny * L values, to out (device memory if out_is_device,

@@ -69,6 +69,9 @@ _SIGS = {
                                _c.POINTER(_c.c_double), _c.POINTER(_c.c_double)]),
     "okz_heights": (_c.c_int, [_vp, _c.c_int64, _c.c_int64, _vp, _c.c_int]),
     "okz_profiles": (_c.c_int, [_vp, _vp, _vp]),
+    "okz_moments_enqueue": (_c.c_int, [_vp]),
+    "okz_moments_fetch": (_c.c_int, [_vp, _c.POINTER(okz_i128), _c.POINTER(_c.c_double),
+                               _c.POINTER(_c.c_double), _c.POINTER(_c.c_double)]),
     "okz_psd": (_c.c_int, [_vp, _vp]),
     "okz_state": (_c.c_int, [_vp, _vp, _c.c_int, _c.POINTER(_c.c_int64),
                              _c.POINTER(_c.c_uint64)]),
@@ -183,6 +186,19 @@ def okz_width2(h):
     _check(lib().okz_width2(h, ctypes.byref(S1), ctypes.byref(S2), ctypes.byref(W2)),
            "okz_width2")
     return S1.value(), S2.value(), W2.value
+
+
+def okz_moments_enqueue(h):
+    _check(lib().okz_moments_enqueue(h), "okz_moments_enqueue")
+
+
+def okz_moments_fetch(h):
+    """-> as okz_moments, for the sums enqueued by okz_moments_enqueue."""
+    Sk = (okz_i128 * 4)()
+    W2, sk, ku = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(lib().okz_moments_fetch(h, Sk, ctypes.byref(W2), ctypes.byref(sk),
+                                   ctypes.byref(ku)), "okz_moments_fetch")
+    return [s.value() for s in Sk], W2.value, sk.value, ku.value
 
 
 def okz_moments(h):
@@ -313,6 +329,12 @@ class Simulation:
 
     def moments(self):
         return okz_moments(self.h)
+
+    def moments_enqueue(self):
+        okz_moments_enqueue(self.h)
+
+    def moments_fetch(self):
+        return okz_moments_fetch(self.h)
 
     def heights(self, y0=0, ny=None, out=None):
         return okz_heights(self.h, y0, self.L - y0 if ny is None else ny, self.L, out)

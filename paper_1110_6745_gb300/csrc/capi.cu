@@ -255,7 +255,9 @@ okz_status okz_create_ex(const okz_params *prm, void *dev_buf, size_t bytes, voi
     else
       e = launch_init_flat(sim->planes[0], prm->L, sim->stream);
   }
-  if (e == cudaSuccess) e = cudaStreamSynchronize(sim->stream);
+  // on a caller's stream the initialisation stays enqueued (stream order covers
+  // every later call); on the library's own stream creation waits for it
+  if (e == cudaSuccess && sim->own_stream) e = cudaStreamSynchronize(sim->stream);
   if (e != cudaSuccess) {
     okz_status r = cuda_fail(e, "initialisation");
     if (sim->own_mem) cudaFree(sim->base);
@@ -379,11 +381,9 @@ okz_status okz_synchronize(okz_sim *sim) {
 
 void *okz_stream(okz_sim *sim) { return sim ? (void *)sim->stream : nullptr; }
 
-// Runs the power-sum kernels and reads back H0 and S_1..S_nmom (about H0).
-static okz_status power_sums(okz_sim *sim, int nmom, long long *H0, __int128 S[4]) {
-  cudaError_t e = launch_power_sums(sim->planes[sim->cur], sim->prm.L, sim->parity, nmom,
-                                    sim->hcol, sim->partials, sim->ctrl, sim->stream);
-  if (e != cudaSuccess) return cuda_fail(e, "power-sum launch");
+// Reads back H0 and S_1..S_4 (about H0) once the stream is done.
+static okz_status read_sums(okz_sim *sim, long long *H0, __int128 S[4]) {
+  cudaError_t e;
   okz_status st = sync_and_check(sim);
   if (st != OKZ_OK) return st;
   Ctrl c;
@@ -394,6 +394,14 @@ static okz_status power_sums(okz_sim *sim, int nmom, long long *H0, __int128 S[4
     S[n] = (__int128)(((unsigned __int128)c.sum[2 * n + 1] << 64) |
                       (unsigned __int128)c.sum[2 * n]);
   return OKZ_OK;
+}
+
+// Runs the power-sum kernels and reads back H0 and S_1..S_nmom (about H0).
+static okz_status power_sums(okz_sim *sim, int nmom, long long *H0, __int128 S[4]) {
+  cudaError_t e = launch_power_sums(sim->planes[sim->cur], sim->prm.L, sim->parity, nmom,
+                                    sim->hcol, sim->partials, sim->ctrl, sim->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "power-sum launch");
+  return read_sums(sim, H0, S);
 }
 
 okz_status okz_width2(okz_sim *sim, okz_i128 *S1, okz_i128 *S2, double *W2) {
@@ -417,8 +425,7 @@ okz_status okz_width2(okz_sim *sim, okz_i128 *S1, okz_i128 *S2, double *W2) {
   return OKZ_OK;
 }
 
-okz_status okz_moments(okz_sim *sim, okz_i128 Sk[4], double *W2, double *skew,
-                       double *kurt) {
+static okz_status moments_check(okz_sim *sim) {
   if (!sim) {
     set_error("null simulation");
     return OKZ_EINVAL;
@@ -427,10 +434,45 @@ okz_status okz_moments(okz_sim *sim, okz_i128 Sk[4], double *W2, double *skew,
     set_error("okz_moments needs L <= 131072");
     return OKZ_EUNSUPPORTED;
   }
+  return OKZ_OK;
+}
+
+static okz_status moments_finish(okz_sim *sim, const __int128 S[4], okz_i128 Sk[4],
+                                 double *W2, double *skew, double *kurt);
+
+okz_status okz_moments(okz_sim *sim, okz_i128 Sk[4], double *W2, double *skew,
+                       double *kurt) {
+  okz_status st = moments_check(sim);
+  if (st != OKZ_OK) return st;
   long long H0 = 0;
   __int128 S[4];
-  okz_status st = power_sums(sim, 4, &H0, S);
+  st = power_sums(sim, 4, &H0, S);
   if (st != OKZ_OK) return st;
+  return moments_finish(sim, S, Sk, W2, skew, kurt);
+}
+
+okz_status okz_moments_enqueue(okz_sim *sim) {
+  okz_status st = moments_check(sim);
+  if (st != OKZ_OK) return st;
+  cudaError_t e = launch_power_sums(sim->planes[sim->cur], sim->prm.L, sim->parity, 4,
+                                    sim->hcol, sim->partials, sim->ctrl, sim->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "power-sum launch");
+  return OKZ_OK;
+}
+
+okz_status okz_moments_fetch(okz_sim *sim, okz_i128 Sk[4], double *W2, double *skew,
+                             double *kurt) {
+  okz_status st = moments_check(sim);
+  if (st != OKZ_OK) return st;
+  long long H0 = 0;
+  __int128 S[4];
+  st = read_sums(sim, &H0, S);
+  if (st != OKZ_OK) return st;
+  return moments_finish(sim, S, Sk, W2, skew, kurt);
+}
+
+static okz_status moments_finish(okz_sim *sim, const __int128 S[4], okz_i128 Sk[4],
+                                 double *W2, double *skew, double *kurt) {
   const __int128 N = (__int128)sim->prm.L * sim->prm.L;
   if (Sk)
     for (int n = 0; n < 4; ++n) Sk[n] = from_i128(S[n]);

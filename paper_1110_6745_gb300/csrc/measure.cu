@@ -7,8 +7,12 @@
 // Only the X plane and column 0 of the Y plane are read (0.125 B/site); on
 // the height-parity plane (parity.cu) the slopes are formed on the fly.
 //
-// Power sums S_n = sum (h - H0)^n are exact: 64-bit per word and per thread,
-// 128-bit per thread total, then per block, then a single-block final sum.
+// A row is read by one warp in chunks of 32 consecutive words (lane l takes
+// word 32c + l, so every load is coalesced); a warp scan of the words'
+// height changes gives each lane the height at the start of its word.
+// Power sums S_n = sum (h - H0)^n are exact: per word from byte tables of
+// the in-byte offsets' powers, combined binomially with the word's start
+// height, 128-bit per thread, then per block, then a single-block final sum.
 #include "okz_internal.h"
 #include "okz_planes.cuh"
 
@@ -16,14 +20,13 @@ namespace okz {
 
 namespace {
 
-__device__ __forceinline__ int warp_exclusive_scan(int v, int lane) {
-  int inc = v;
+__device__ __forceinline__ int warp_inclusive_scan(int v, int lane) {
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const int n = __shfl_up_sync(0xFFFFFFFFu, inc, o);
-    if (lane >= o) inc += n;
+    const int n = __shfl_up_sync(0xFFFFFFFFu, v, o);
+    if (lane >= o) v += n;
   }
-  return inc - v;
+  return v;
 }
 
 __device__ __forceinline__ long long warp_exclusive_scan64(long long v, int lane) {
@@ -36,21 +39,53 @@ __device__ __forceinline__ long long warp_exclusive_scan64(long long v, int lane
   return inc - v;
 }
 
+// Column-0 slope bits of rows 32j .. 32j+31 (bit k = [sigma_y(0, 32j+k) = +1]).
+template <bool PAR>
+__device__ __forceinline__ uint32_t col0_word(const uint32_t *__restrict__ P, int64_t L,
+                                              int64_t W, int64_t j) {
+  uint32_t c[33];
+  const int64_t y0 = 32 * j;
+  if (PAR) {
+#pragma unroll
+    for (int k = 0; k < 33; ++k) {
+      int64_t y = y0 + k;
+      if (y >= L) y -= L;
+      c[k] = P[y * W];
+    }
+    uint32_t m = 0;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) m |= (~(c[k] ^ c[k + 1] ^ (uint32_t)((y0 + k) & 1)) & 1u) << k;
+    return m;
+  }
+  const uint32_t *Yp = P + L * W;
+#pragma unroll
+  for (int k = 0; k < 32; ++k) c[k] = Yp[(y0 + k) * W];
+  uint32_t m = 0;
+#pragma unroll
+  for (int k = 0; k < 32; ++k) m |= (c[k] & 1u) << k;
+  return m;
+}
+
 }  // namespace
 
-// hcol[y] = h(0,y) - H0 = sum_{y'<y} sigma_y(0,y'): one block, each thread a
-// contiguous run of rows, block-wide exclusive scan of the run totals.
+// hcol[y] = h(0,y) - H0 = sum_{y'<y} sigma_y(0,y'): one block. The column's
+// slope bits are gathered into shared memory first (33 independent loads per
+// 32 rows, so many are in flight), then each thread scans a contiguous run.
 template <bool PAR>
 __global__ void __launch_bounds__(1024)
 colscan_kernel(const uint32_t *__restrict__ planes, int64_t L, int64_t *__restrict__ hcol) {
+  extern __shared__ uint32_t col_bits[];  // L/32 words
   __shared__ long long warp_tot[32];
   const int64_t W = L >> 5;
+  const int64_t nw32 = L >> 5;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int64_t R = (L + blockDim.x - 1) / blockDim.x;
-  const int64_t y0 = tid * R < L ? tid * R : L;
-  const int64_t y1 = y0 + R < L ? y0 + R : L;
+  for (int64_t j = tid; j < nw32; j += blockDim.x) col_bits[j] = col0_word<PAR>(planes, L, W, j);
+  __syncthreads();
+  const int64_t R = (nw32 + blockDim.x - 1) / blockDim.x;  // words per thread
+  const int64_t j0 = tid * R < nw32 ? tid * R : nw32;
+  const int64_t j1 = j0 + R < nw32 ? j0 + R : nw32;
   long long run = 0;
-  for (int64_t y = y0; y < y1; ++y) run += 2 * (long long)col0_up<PAR>(planes, L, W, y) - 1;
+  for (int64_t j = j0; j < j1; ++j) run += 2LL * __popc(col_bits[j]) - 32;
   const long long pre = warp_exclusive_scan64(run, lane);
   if (lane == 31) warp_tot[warp] = pre + run;
   __syncthreads();
@@ -62,43 +97,51 @@ colscan_kernel(const uint32_t *__restrict__ planes, int64_t L, int64_t *__restri
   }
   __syncthreads();
   long long h = warp_tot[warp] + pre;
-  for (int64_t y = y0; y < y1; ++y) {
-    hcol[y] = h;
-    h += 2 * (long long)col0_up<PAR>(planes, L, W, y) - 1;
+  for (int64_t j = j0; j < j1; ++j) {
+    const uint32_t m = col_bits[j];
+    for (int k = 0; k < 32; ++k) {
+      hcol[32 * j + k] = h;
+      h += 2 * (long long)((m >> k) & 1u) - 1;
+    }
   }
 }
 
-// Byte table for the within-word sums: for byte value v and offsets
-// e_0 = 0, e_{b+1} = e_b + 2 v_b - 1 (b = 0..7): cnt = popcount(v),
-// A = sum e_b in [-28, 28], B = sum e_b^2 in [0, 140];
-// packed as cnt | (A + 28) << 4 | B << 10.
-__device__ __forceinline__ uint32_t byte_entry(uint32_t v) {
-  int e = 0, A = 0, B = 0;
+// Byte tables for the within-word sums: for byte value v and in-byte offsets
+// e_0 = 0, e_{b+1} = e_b + 2 v_b - 1 (b = 0..7), T_n = sum_b e_b^n:
+//   A = popcount(v) | (T1 + 28) << 4 | T2 << 10        (T1 in [-28, 28], T2 <= 140)
+//   B = (T3 + 784) | T4 << 11                          (|T3| <= 784, T4 <= 4676)
+__device__ __forceinline__ void byte_entries(uint32_t v, uint32_t &A, uint32_t &B) {
+  int e = 0, t1 = 0, t2 = 0, t3 = 0, t4 = 0;
   for (int b = 0; b < 8; ++b) {
-    A += e;
-    B += e * e;
+    t1 += e;
+    t2 += e * e;
+    t3 += e * e * e;
+    t4 += e * e * e * e;
     e += 2 * (int)((v >> b) & 1u) - 1;
   }
-  return (uint32_t)__popc(v) | ((uint32_t)(A + 28) << 4) | ((uint32_t)B << 10);
+  A = (uint32_t)__popc(v) | ((uint32_t)(t1 + 28) << 4) | ((uint32_t)t2 << 10);
+  B = (uint32_t)(t3 + 784) | ((uint32_t)t4 << 11);
 }
 
-// Row sums. Each warp owns rows y = warp id, warp id + #warps, ...; lane l
-// owns the contiguous words [l*wpl, (l+1)*wpl) of the row. NMOM = 2 gives
-// S1, S2 with the byte table; NMOM = 4 gives S1..S4 with a bit loop.
+// Row sums: each warp owns rows y = warp id, warp id + #warps, ... NMOM = 2
+// gives S1, S2; NMOM = 4 gives S1..S4.
 template <int NMOM, bool PAR>
 __global__ void __launch_bounds__(256)
 rowsum_kernel(const uint32_t *__restrict__ Xp, int64_t L,
               const int64_t *__restrict__ hcol, unsigned long long *__restrict__ partials) {
-  __shared__ uint32_t tab[256];
+  __shared__ uint32_t tabA[256], tabB[256];
   __shared__ __int128 red[NMOM][256];
   const int tid = threadIdx.x, lane = tid & 31;
-  tab[tid] = byte_entry(tid);
+  {
+    uint32_t A, B;
+    byte_entries(tid, A, B);
+    tabA[tid] = A;
+    tabB[tid] = B;
+  }
   __syncthreads();
 
   const int64_t W = L >> 5;
-  const int64_t wpl = (W + 31) >> 5;
-  const int64_t w0 = lane * wpl < W ? lane * wpl : W;
-  const int64_t w1 = w0 + wpl < W ? w0 + wpl : W;
+  const int64_t nch = (W + 31) >> 5;
   const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + tid) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
 
@@ -108,48 +151,131 @@ rowsum_kernel(const uint32_t *__restrict__ Xp, int64_t L,
 
   for (int64_t y = gwarp; y < L; y += nwarps) {
     const uint32_t *row = Xp + y * W;
-    int c = 0;
-    for (int64_t w = w0; w < w1; ++w) c += __popc(x_word<PAR>(row, W, w, y));
-    const int d = 2 * c - 32 * (int)(w1 - w0);  // height change over my words
-    long long a = hcol[y] + warp_exclusive_scan(d, lane);
-    long long s1 = 0, s2 = 0;
-    for (int64_t w = w0; w < w1; ++w) {
-      const uint32_t v = x_word<PAR>(row, W, w, y);
-      if (NMOM == 2) {
-        long long es = 0, eq = 0;
-        int o = 0;
+    long long carry = hcol[y];
+    long long r1 = 0, r2 = 0;  // this row's S1, S2 (they fit 64 bits)
+    for (int64_t c = 0; c < nch; ++c) {
+      const int64_t w = 32 * c + lane;
+      const bool on = w < W;
+      const uint32_t v = on ? x_word<PAR>(row, W, w, y) : 0u;
+      const int d = on ? 2 * __popc(v) - 32 : 0;
+      const int incl = warp_inclusive_scan(d, lane);
+      const long long a = carry + (incl - d);  // height at the start of word w
+      carry += __shfl_sync(0xFFFFFFFFu, incl, 31);
+      if (!on) continue;
+      int E1 = 0, E2 = 0, E3 = 0, E4 = 0, o = 0;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const uint32_t T = tab[(v >> (8 * i)) & 0xFFu];
-          const int A = (int)((T >> 4) & 63u) - 28;
-          const int B = (int)(T >> 10);
-          es += 8 * o + A;
-          eq += 8 * o * o + 2 * o * A + B;
-          o += 2 * (int)(T & 15u) - 8;
+      for (int i = 0; i < 4; ++i) {
+        const uint32_t byte = (v >> (8 * i)) & 0xFFu;
+        const uint32_t A = tabA[byte];
+        const int T1 = (int)((A >> 4) & 63u) - 28, T2 = (int)(A >> 10);
+        E1 += 8 * o + T1;
+        E2 += 8 * o * o + 2 * o * T1 + T2;
+        if (NMOM == 4) {
+          const uint32_t B = tabB[byte];
+          const int T3 = (int)(B & 2047u) - 784, T4 = (int)(B >> 11);
+          E3 += 8 * o * o * o + 3 * o * o * T1 + 3 * o * T2 + T3;
+          E4 += 8 * o * o * o * o + 4 * o * o * o * T1 + 6 * o * o * T2 + 4 * o * T3 + T4;
         }
-        s1 += 32 * a + es;
-        s2 += 32 * a * a + 2 * a * es + eq;
-        a += 2 * __popc(v) - 32;
-      } else {
-        for (int b = 0; b < 32; ++b) {
-          const __int128 h = a;
-          s[0] += h;
-          s[1] += h * h;
-          s[2] += h * h * h;
-          s[3] += h * h * h * h;
-          a += 2 * (long long)((v >> b) & 1u) - 1;
-        }
+        o += 2 * (int)(A & 15u) - 8;
+      }
+      // sum over the word of (a + e)^n, |a| <= L, binomially
+      const long long a2 = a * a;
+      r1 += 32 * a + E1;
+      r2 += 32 * a2 + 2 * a * E1 + E2;
+      if (NMOM == 4) {
+        const long long a3 = a2 * a;  // |a|^3 <= 2^51 for L <= 2^17
+        s[2] += (__int128)(32 * a3) + (__int128)(3 * a2) * E1 + (__int128)(3 * a) * E2 + E3;
+        s[3] += (__int128)a2 * (32 * a2) + (__int128)(4 * a3) * E1 +
+                (__int128)(6 * a2) * E2 + (__int128)(4 * a) * E3 + E4;
       }
     }
-    if (NMOM == 2) {
-      s[0] += s1;
-      s[1] += s2;
-    }
+    s[0] += r1;
+    s[1] += r2;
   }
 #pragma unroll
   for (int n = 0; n < NMOM; ++n) red[n][tid] = s[n];
   __syncthreads();
   if (tid < NMOM) {
+    __int128 tot = 0;
+    for (int i = 0; i < 256; ++i) tot += red[tid][i];
+    partials[blockIdx.x * 8 + 2 * tid] = (unsigned long long)tot;
+    partials[blockIdx.x * 8 + 2 * tid + 1] = (unsigned long long)(tot >> 64);
+  }
+}
+
+// S1, S2 for rows of a multiple of 128 words (L % 4096 == 0): lane l takes
+// the four words 128c + 4l .. 128c + 4l + 3 of chunk c as one 16-byte load,
+// so the warp scan runs once per four words, and the lane's sums are formed
+// relative to its own start height (32-bit) and shifted once per chunk.
+template <bool PAR>
+__global__ void __launch_bounds__(256)
+rowsum4_kernel(const uint32_t *__restrict__ Xp, int64_t L,
+               const int64_t *__restrict__ hcol, unsigned long long *__restrict__ partials) {
+  __shared__ uint32_t tabA[256];
+  __shared__ __int128 red[2][256];
+  const int tid = threadIdx.x, lane = tid & 31;
+  {
+    uint32_t A, B;
+    byte_entries(tid, A, B);
+    tabA[tid] = A;
+  }
+  __syncthreads();
+  const int64_t W = L >> 5;
+  const int64_t nch = W >> 7;
+  const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + tid) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  __int128 s1 = 0, s2 = 0;
+  for (int64_t y = gwarp; y < L; y += nwarps) {
+    const uint32_t *row = Xp + y * W;
+    const uint32_t odd = odd_sites(y);
+    long long carry = hcol[y];
+    long long r1 = 0, r2 = 0;
+    for (int64_t c = 0; c < nch; ++c) {
+      const int64_t w0 = 128 * c + 4 * lane;
+      const uint4 q = *reinterpret_cast<const uint4 *>(row + w0);
+      uint32_t v[4] = {q.x, q.y, q.z, q.w};
+      if (PAR) {  // X bits from the parity bits: ~(b ^ b(x+1) ^ p)
+        uint32_t nxt = __shfl_down_sync(0xFFFFFFFFu, q.x, 1);
+        if (lane == 31) nxt = row[(w0 + 4 == W) ? 0 : w0 + 4];
+        const uint32_t n[4] = {q.y, q.z, q.w, nxt};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) v[j] = ~(v[j] ^ __funnelshift_r(v[j], n[j], 1) ^ odd);
+      }
+      int dj[4], dsum = 0;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        dj[j] = 2 * __popc(v[j]) - 32;
+        dsum += dj[j];
+      }
+      const int incl = warp_inclusive_scan(dsum, lane);
+      const long long A0 = carry + (incl - dsum);  // height at the start of word w0
+      carry += __shfl_sync(0xFFFFFFFFu, incl, 31);
+      int s1r = 0, s2r = 0, ap = 0;  // sums relative to A0; ap = offset of word j
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        int E1 = 0, E2 = 0, o = 0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const uint32_t A = tabA[(v[j] >> (8 * i)) & 0xFFu];
+          const int T1 = (int)((A >> 4) & 63u) - 28, T2 = (int)(A >> 10);
+          E1 += 8 * o + T1;
+          E2 += 8 * o * o + 2 * o * T1 + T2;
+          o += 2 * (int)(A & 15u) - 8;
+        }
+        s1r += 32 * ap + E1;
+        s2r += 32 * ap * ap + 2 * ap * E1 + E2;
+        ap += dj[j];
+      }
+      r1 += 128 * A0 + s1r;
+      r2 += 128 * A0 * A0 + 2 * A0 * s1r + s2r;
+    }
+    s1 += r1;
+    s2 += r2;
+  }
+  red[0][tid] = s1;
+  red[1][tid] = s2;
+  __syncthreads();
+  if (tid < 2) {
     __int128 tot = 0;
     for (int i = 0; i < 256; ++i) tot += red[tid][i];
     partials[blockIdx.x * 8 + 2 * tid] = (unsigned long long)tot;
@@ -182,33 +308,46 @@ partials_sum_kernel(const unsigned long long *__restrict__ partials, int nblocks
   }
 }
 
-cudaError_t launch_colscan(const uint32_t *planes, int64_t L, bool parity, int64_t *hcol,
-                           cudaStream_t st) {
-  if (parity)
-    colscan_kernel<true><<<1, 1024, 0, st>>>(planes, L, hcol);
-  else
-    colscan_kernel<false><<<1, 1024, 0, st>>>(planes, L, hcol);
-  return cudaGetLastError();
-}
-
 static int reduce_blocks(int64_t L) {
   int64_t b = (L + 7) / 8;  // 8 warps per block, one row per warp
   if (b > kMaxReduceBlocks) b = kMaxReduceBlocks;
   return (int)b;
 }
 
+cudaError_t launch_colscan(const uint32_t *planes, int64_t L, bool parity, int64_t *hcol,
+                           cudaStream_t st) {
+  const size_t smem = (size_t)(L >> 5) * sizeof(uint32_t);
+  if (parity) {
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(colscan_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem);
+    colscan_kernel<true><<<1, 1024, smem, st>>>(planes, L, hcol);
+  } else {
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(colscan_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem);
+    colscan_kernel<false><<<1, 1024, smem, st>>>(planes, L, hcol);
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_power_sums(const uint32_t *planes, int64_t L, bool parity, int nmom,
                               int64_t *hcol, unsigned long long *partials, Ctrl *ctrl,
                               cudaStream_t st) {
   const int nb = reduce_blocks(L);
-  if (parity) {
-    colscan_kernel<true><<<1, 1024, 0, st>>>(planes, L, hcol);
+  cudaError_t e = launch_colscan(planes, L, parity, hcol, st);
+  if (e != cudaSuccess) return e;
+  if (nmom == 2 && L % 4096 == 0) {
+    if (parity)
+      rowsum4_kernel<true><<<nb, 256, 0, st>>>(planes, L, hcol, partials);
+    else
+      rowsum4_kernel<false><<<nb, 256, 0, st>>>(planes, L, hcol, partials);
+  } else if (parity) {
     if (nmom == 2)
       rowsum_kernel<2, true><<<nb, 256, 0, st>>>(planes, L, hcol, partials);
     else
       rowsum_kernel<4, true><<<nb, 256, 0, st>>>(planes, L, hcol, partials);
   } else {
-    colscan_kernel<false><<<1, 1024, 0, st>>>(planes, L, hcol);
     if (nmom == 2)
       rowsum_kernel<2, false><<<nb, 256, 0, st>>>(planes, L, hcol, partials);
     else
@@ -219,16 +358,18 @@ cudaError_t launch_power_sums(const uint32_t *planes, int64_t L, bool parity, in
 }
 
 // h(x, y0 + r) for r < ny as int32, row-major; flags heights outside int32.
+// Each warp computes a chunk of 32 words (1024 heights) into shared memory
+// and writes it out with coalesced stores.
 template <bool PAR>
 __global__ void __launch_bounds__(256)
 heights_kernel(const uint32_t *__restrict__ Xp, int64_t L, int64_t y0, int64_t ny,
                const int64_t *__restrict__ hcol, int32_t *__restrict__ out,
                Ctrl *__restrict__ ctrl) {
-  const int lane = threadIdx.x & 31;
+  __shared__ int32_t stage[8][1024 + 32];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  int32_t *sm = stage[wib];
   const int64_t W = L >> 5;
-  const int64_t wpl = (W + 31) >> 5;
-  const int64_t w0 = lane * wpl < W ? lane * wpl : W;
-  const int64_t w1 = w0 + wpl < W ? w0 + wpl : W;
+  const int64_t nch = (W + 31) >> 5;
   const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const long long H0 = ctrl->H0;
@@ -236,18 +377,26 @@ heights_kernel(const uint32_t *__restrict__ Xp, int64_t L, int64_t y0, int64_t n
   for (int64_t r = gwarp; r < ny; r += nwarps) {
     const int64_t y = y0 + r;
     const uint32_t *row = Xp + y * W;
-    int c = 0;
-    for (int64_t w = w0; w < w1; ++w) c += __popc(x_word<PAR>(row, W, w, y));
-    const int d = 2 * c - 32 * (int)(w1 - w0);
-    long long h = H0 + hcol[y] + warp_exclusive_scan(d, lane);
     int32_t *o = out + r * L;
-    for (int64_t w = w0; w < w1; ++w) {
-      const uint32_t v = x_word<PAR>(row, W, w, y);
+    long long carry = H0 + hcol[y];
+    for (int64_t c = 0; c < nch; ++c) {
+      const int64_t w = 32 * c + lane;
+      const bool on = w < W;
+      const uint32_t v = on ? x_word<PAR>(row, W, w, y) : 0u;
+      const int d = on ? 2 * __popc(v) - 32 : 0;
+      const int incl = warp_inclusive_scan(d, lane);
+      long long h = carry + (incl - d);
+      carry += __shfl_sync(0xFFFFFFFFu, incl, 31);
+      // lane's 32 heights at sm[33 * lane + b] (padded: conflict-free)
       for (int b = 0; b < 32; ++b) {
-        bad |= (h < INT32_MIN) || (h > INT32_MAX);
-        o[32 * w + b] = (int32_t)h;
+        bad |= on && ((h < INT32_MIN) || (h > INT32_MAX));
+        sm[33 * lane + b] = (int32_t)h;
         h += 2 * (long long)((v >> b) & 1u) - 1;
       }
+      __syncwarp();
+      const int64_t nvalid = (W - 32 * c < 32 ? W - 32 * c : 32) * 32;  // heights in chunk
+      for (int k = lane; k < nvalid; k += 32) o[1024 * c + k] = sm[33 * (k >> 5) + (k & 31)];
+      __syncwarp();
     }
   }
   if (bad) atomicOr(&ctrl->err, kErrHeightRange);
@@ -259,13 +408,12 @@ cudaError_t launch_heights(const uint32_t *planes, int64_t L, bool parity, int64
   int64_t nb = (ny + 7) / 8;
   if (nb > 152 * 16) nb = 152 * 16;
   if (nb < 1) nb = 1;
-  if (parity) {
-    colscan_kernel<true><<<1, 1024, 0, st>>>(planes, L, hcol);
+  cudaError_t e = launch_colscan(planes, L, parity, hcol, st);
+  if (e != cudaSuccess) return e;
+  if (parity)
     heights_kernel<true><<<(unsigned)nb, 256, 0, st>>>(planes, L, y0, ny, hcol, out, ctrl);
-  } else {
-    colscan_kernel<false><<<1, 1024, 0, st>>>(planes, L, hcol);
+  else
     heights_kernel<false><<<(unsigned)nb, 256, 0, st>>>(planes, L, y0, ny, hcol, out, ctrl);
-  }
   return cudaGetLastError();
 }
 

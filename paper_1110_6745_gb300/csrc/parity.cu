@@ -110,99 +110,6 @@ cudaError_t launch_parity_halfsweep(uint32_t *B, int64_t L, int s, uint32_t t, u
 }
 
 // ---------------------------------------------------------------------------
-// Domain-decomposed random-sequential sweeps (the paper's own GPU dynamics,
-// Sec. II: blocks with dead borders, the origin moved at random every MCS,
-// random update attempts inside each block). Sweep t: offsets (ox, oy) =
-// (r0, r1) mod 32 of Philox(ctr = (0, 0, t, 768)); 32 x 32 cells with origins
-// (ox + 32i, oy + 32j) mod L and ids c = j*(L/32) + i; cell c receives 1024
-// attempts, attempt a drawing words (r0, r1) (a even) or (r2, r3) (a odd) of
-// Philox(ctr = (c, a/2, t, 1024)): local x = first & 31, local y =
-// (first >> 16) & 31, u = second; attempts on the dead first column or first
-// row do nothing, otherwise a minimum moves iff u < P32 and a maximum iff
-// u < Q32. As in Fig. 1 of the paper two dead edges suffice: a cell's last
-// column and row read only the next cells' dead first column and row, which
-// do not change during the sweep. One thread per cell: the cell (33 rows of
-// 33 bits: its own sites plus those frozen neighbours) is staged in shared
-// memory, swept, and its changed bits are xor-ed back (neighbouring cells
-// share the words at their x edges).
-// ---------------------------------------------------------------------------
-constexpr int kCell = 32;
-constexpr int kCellStride = kCell + 3;  // rows 0..32, then the column x0+32; odd stride
-
-__global__ void __launch_bounds__(128)
-ddrs_kernel(uint32_t *__restrict__ B, int L, uint32_t t, const RoundKeys rk, uint64_t P32,
-            uint64_t Q32, Ctrl *__restrict__ ctrl) {
-  __shared__ uint32_t cell_sm[128][kCellStride];
-  uint32_t *cell = cell_sm[threadIdx.x];
-  const int ncell = L / kCell;
-  const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= (uint32_t)ncell * (uint32_t)ncell) return;
-  const u32x4 o = philox10_rk(0u, 0u, t, 768u, rk);
-  const int ox = (int)(o.v[0] & (kCell - 1)), oy = (int)(o.v[1] & (kCell - 1));
-  const int ci = (int)(c % (uint32_t)ncell), cj = (int)(c / (uint32_t)ncell);
-  const int x0 = (ox + ci * kCell) % L, y0 = (oy + cj * kCell) % L;
-  const int W = L >> 5;
-  const int wA = x0 >> 5, sh = x0 & 31, wB = (wA + 1 == W) ? 0 : wA + 1;
-  uint32_t next_col = 0;  // bit ly = b(x0 + 32, y0 + ly)
-  for (int ly = 0; ly <= kCell; ++ly) {
-    const int y = (y0 + ly) % L;
-    const uint32_t a = B[(size_t)y * W + wA], b = B[(size_t)y * W + wB];
-    cell[ly] = __funnelshift_r(a, b, sh);
-    if (ly < kCell) next_col |= ((b >> sh) & 1u) << ly;
-  }
-  uint32_t touched = 0;
-  int dH0 = 0;
-  uint32_t r2 = 0, r3 = 0;
-  for (uint32_t a = 0; a < kCell * kCell; ++a) {
-    uint32_t first, u;
-    if ((a & 1u) == 0) {
-      const u32x4 r = philox10_rk(c, a >> 1, t, 1024u, rk);
-      first = r.v[0];
-      u = r.v[1];
-      r2 = r.v[2];
-      r3 = r.v[3];
-    } else {
-      first = r2;
-      u = r3;
-    }
-    const int lx = (int)(first & (kCell - 1)), ly = (int)((first >> 16) & (kCell - 1));
-    if (lx == 0 || ly == 0) continue;  // dead border
-    const int x = (x0 + lx) % L, y = (y0 + ly) % L;
-    const uint32_t row = cell[ly];
-    const uint32_t cc = ((row >> lx) ^ (uint32_t)(x + y)) & 1u;  // own bit ^ parity
-    const uint32_t l = (row >> (lx - 1)) & 1u;
-    const uint32_t r = (lx == kCell - 1) ? (next_col >> ly) & 1u : (row >> (lx + 1)) & 1u;
-    const uint32_t dn = (cell[ly - 1] >> lx) & 1u, up = (cell[ly + 1] >> lx) & 1u;
-    const bool is_min = l == cc && r == cc && dn == cc && up == cc;
-    const bool is_max = l != cc && r != cc && dn != cc && up != cc;
-    const bool accept = (is_min && (uint64_t)u < P32) || (is_max && (uint64_t)u < Q32);
-    if (!accept) continue;
-    cell[ly] = row ^ (1u << lx);
-    touched |= 1u << ly;
-    if (x == 0 && y == 0) dH0 += is_min ? 2 : -2;
-  }
-  while (touched) {
-    const int ly = __ffs(touched) - 1;
-    touched &= touched - 1;
-    const int y = (y0 + ly) % L;
-    uint32_t *pa = B + (size_t)y * W + wA, *pb = B + (size_t)y * W + wB;
-    const uint32_t old = __funnelshift_r(*pa, *pb, sh);  // this cell's bits are its own
-    const uint32_t delta = old ^ cell[ly];
-    atomicXor(pa, delta << sh);
-    if (sh) atomicXor(pb, delta >> (32 - sh));
-  }
-  if (dH0) atomicAdd((unsigned long long *)&ctrl->H0, (unsigned long long)(long long)dH0);
-}
-
-cudaError_t launch_ddrs(uint32_t *B, int64_t L, uint32_t t, uint64_t seed, uint64_t P32,
-                        uint64_t Q32, Ctrl *ctrl, cudaStream_t st) {
-  const int64_t cells = (L / kCell) * (L / kCell);
-  ddrs_kernel<<<(unsigned)((cells + 127) / 128), 128, 0, st>>>(B, (int)L, t, round_keys(seed),
-                                                              P32, Q32, ctrl);
-  return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------------------
 // Boundary conversions.
 // ---------------------------------------------------------------------------
 __global__ void to_slopes_kernel(const uint32_t *__restrict__ B, int64_t L,
@@ -339,12 +246,13 @@ struct PModes {
 // tests use 3-input logic: for SP = 0 a minimum has all four neighbours equal
 // to its own bit ("both equal" table 0x81 on (l, r, c) and on (d, u, c)),
 // for SP = 1 all four differ (table 0x42); maxima are the reverse.
-template <int WPT, int MODE, int SP>
+template <int WPT, int MODE, int SP, int KC>
 __device__ __forceinline__ void pstage(const uint32_t c[WPT], uint32_t lbit, uint32_t rbit,
                                        const uint32_t d[WPT], const uint32_t u[WPT], uint32_t a,
-                                       const uint32_t r0[WPT], uint32_t g0, uint32_t t,
+                                       const uint32_t (&lv)[KC][WPT], uint32_t g0, uint32_t t,
                                        const RoundKeys &rk, const Accept &acc,
                                        const PModes &md, uint32_t f[WPT], uint32_t *mn0) {
+  const uint32_t *r0 = lv[0];
   constexpr uint32_t kMin = SP ? 0x42u : 0x81u;
   constexpr uint32_t kMax = SP ? 0x81u : 0x42u;
   uint32_t mn[WPT], mx[WPT];
@@ -355,13 +263,15 @@ __device__ __forceinline__ void pstage(const uint32_t c[WPT], uint32_t lbit, uin
     if (MODE == kPModeHalf) {
       const uint32_t ar = a & ~r0[j];  // active and selected by the level-0 bit
       f[j] = lop3<0x80>(lop3<kMin>(l, r, c[j]), lop3<kMin>(d[j], u[j], c[j]), ar);
-      if (j == 0) *mn0 = lop3<0x80>(lop3<kMin>(l, r, c[j]), lop3<kMin>(d[j], u[j], c[j]), a);
     } else {
       mn[j] = lop3<0x80>(lop3<kMin>(l, r, c[j]), lop3<kMin>(d[j], u[j], c[j]), a);
       mx[j] = lop3<0x80>(lop3<kMax>(l, r, c[j]), lop3<kMax>(d[j], u[j], c[j]), a);
     }
   }
-  if (MODE == kPModeHalf) return;
+  if (MODE == kPModeHalf) {  // q = 0: every move is a minimum rising by 2
+    *mn0 = 1u;
+    return;
+  }
   *mn0 = mn[0];
   if (MODE == kPModeK1) {
 #pragma unroll
@@ -381,9 +291,12 @@ __device__ __forceinline__ void pstage(const uint32_t c[WPT], uint32_t lbit, uin
     }
     for (int m = 0; m < acc.k && any != 0u; ++m) {
       uint32_t rr[WPT];
-      if (m == 0) {
+      if (m < KC) {  // levels drawn once per sweep and carried between its stages
 #pragma unroll
-        for (int j = 0; j < WPT; ++j) rr[j] = r0[j];
+        for (int mm = 0; mm < KC; ++mm)
+          if (mm == m)
+#pragma unroll
+            for (int j = 0; j < WPT; ++j) rr[j] = lv[mm][j];
       } else {
 #pragma unroll
         for (int gq = 0; gq < WPT / 4; ++gq) {
@@ -409,14 +322,18 @@ __device__ __forceinline__ void pstage(const uint32_t c[WPT], uint32_t lbit, uin
 
 }  // namespace
 
-template <int WPT, int F, int MODE>
-__global__ void __launch_bounds__(WPT == 4 ? 1024 : 512, 1)
+// SMALL: rows of at most 256 threads (L <= 32768 at 4 words per thread), so
+// the register budget is not capped by a 1024-thread bound; in the general-k
+// mode these kernels also carry random levels 1 and 2 between half-sweeps.
+template <int WPT, int F, int MODE, bool SMALL>
+__global__ void __launch_bounds__(SMALL ? 256 : (WPT == 4 ? 1024 : 512), 1)
 parity_stream_kernel(const uint32_t *__restrict__ src, uint32_t *__restrict__ dst, int L,
                      int stages, uint32_t t0, const RoundKeys rk, Accept acc, PModes md,
                      Ctrl *__restrict__ ctrl) {
   constexpr int NST = 2 * F;
   constexpr int NC = NST > 1 ? NST - 1 : 1;  // stages whose output is carried
   constexpr int NG = WPT / 4;
+  constexpr int KC = (SMALL && MODE == kPModeGen) ? 3 : 1;  // levels drawn once per sweep
   extern __shared__ __align__(128) unsigned char smem[];
   const int nthr = blockDim.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -455,7 +372,7 @@ parity_stream_kernel(const uint32_t *__restrict__ src, uint32_t *__restrict__ ds
 
   uint32_t Wd[NC][WPT], Wc[NC][WPT];  // stage h's outputs two / one steps ago
   uint32_t WL[NC], WR[NC];            // x-neighbour bits of Wc[h]
-  uint32_t R[F][WPT];                 // level-0 words of the row stage 2j saw last step
+  uint32_t R[F][KC][WPT];             // levels 0..KC-1 of the row stage 2j saw last step
 #pragma unroll
   for (int h = 0; h < NC; ++h) {
     WL[h] = 0;
@@ -469,7 +386,9 @@ parity_stream_kernel(const uint32_t *__restrict__ src, uint32_t *__restrict__ ds
 #pragma unroll
   for (int q = 0; q < F; ++q)
 #pragma unroll
-    for (int j = 0; j < WPT; ++j) R[q][j] = 0;
+    for (int m = 0; m < KC; ++m)
+#pragma unroll
+      for (int j = 0; j < WPT; ++j) R[q][m][j] = 0;
 
   const uint32_t w0 = (uint32_t)(WPT * tid);
   const uint32_t wprev = (w0 == 0) ? W - 1 : w0 - 1;
@@ -508,19 +427,23 @@ parity_stream_kernel(const uint32_t *__restrict__ src, uint32_t *__restrict__ ds
       }
       const uint32_t lb = *(const uint32_t *)(rc + 4 * wprev) >> 31;
       const uint32_t rb = *(const uint32_t *)(rc + 4 * wnext) & 1u;
-      uint32_t Rn[F][WPT];
+      uint32_t Rn[F][KC][WPT];
 #pragma unroll
       for (int h = 0; h < NST; ++h) {
         const int s = h & 1;
         const uint32_t t = t0 + (uint32_t)(h >> 1);
         uint32_t g0 = gq0 - (uint32_t)h * groups_per_row;  // row y-1-h, wrapped
         if (q0 < h) g0 += wrap_groups;
-        if (s == 0) {  // fresh level-0 words of row y-1-h, sweep t
+        if (s == 0) {  // fresh words of row y-1-h, sweep t: level 0, and 1..KC-1 if k needs them
 #pragma unroll
-          for (int gq = 0; gq < NG; ++gq) {
-            const u32x4 b = philox10_rk(g0 + gq, 0u, t, 0u, rk);
+          for (int m = 0; m < KC; ++m) {
+            if (m > 0 && m >= acc.k) break;
 #pragma unroll
-            for (int j = 0; j < 4; ++j) Rn[h >> 1][4 * gq + j] = b.v[j];
+            for (int gq = 0; gq < NG; ++gq) {
+              const u32x4 b = philox10_rk(g0 + gq, 0u, t, (uint32_t)m, rk);
+#pragma unroll
+              for (int j = 0; j < 4; ++j) Rn[h >> 1][m][4 * gq + j] = b.v[j];
+            }
           }
         }
         const uint32_t *c = (h == 0) ? cc : Wc[h > 0 ? h - 1 : 0];
@@ -531,17 +454,19 @@ parity_stream_kernel(const uint32_t *__restrict__ src, uint32_t *__restrict__ ds
         uint32_t f[WPT];
         // s = 1 uses the words of the same row drawn by stage h-1 last step
         if (s == 0)
-          pstage<WPT, MODE, 0>(c, lbit, rbit, d, u, am, Rn[h >> 1], g0, t, rk, acc, md, f,
-                               &mn0[h]);
+          pstage<WPT, MODE, 0, KC>(c, lbit, rbit, d, u, am, Rn[h >> 1], g0, t, rk, acc, md,
+                                   f, &mn0[h]);
         else
-          pstage<WPT, MODE, 1>(c, lbit, rbit, d, u, am, R[h >> 1], g0, t, rk, acc, md, f,
-                               &mn0[h]);
+          pstage<WPT, MODE, 1, KC>(c, lbit, rbit, d, u, am, R[h >> 1], g0, t, rk, acc, md,
+                                   f, &mn0[h]);
         fbit[h] = f[0] & 1u;
 #pragma unroll
         for (int j = 0; j < WPT; ++j) out[h][j] = c[j] ^ f[j];
         if (s == 1) {
 #pragma unroll
-          for (int j = 0; j < WPT; ++j) R[h >> 1][j] = Rn[h >> 1][j];
+          for (int m = 0; m < KC; ++m)
+#pragma unroll
+            for (int j = 0; j < WPT; ++j) R[h >> 1][m][j] = Rn[h >> 1][m][j];
         }
       }
       // H0 = h(0,0): site (0,0) moves in the s = 0 stages; only CTA 0 meets
@@ -657,17 +582,17 @@ PPlan pplan_for(int L, int wpt, const void *fn) {
   return p;
 }
 
-template <int WPT, int F, int MODE>
+template <int WPT, int F, int MODE, bool SMALL = false>
 cudaError_t plaunch(const uint32_t *src, uint32_t *dst, int L, uint32_t t, uint64_t seed,
                     const Accept &acc, const PModes &md, Ctrl *ctrl, cudaStream_t st) {
   static thread_local int cached_L = 0;
   static thread_local PPlan plan;
-  const void *fn = (const void *)parity_stream_kernel<WPT, F, MODE>;
+  const void *fn = (const void *)parity_stream_kernel<WPT, F, MODE, SMALL>;
   if (cached_L != L) {
     plan = pplan_for(L, WPT, fn);
     cached_L = L;
   }
-  parity_stream_kernel<WPT, F, MODE><<<plan.grid, plan.threads, plan.smem, st>>>(
+  parity_stream_kernel<WPT, F, MODE, SMALL><<<plan.grid, plan.threads, plan.smem, st>>>(
       src, dst, L, plan.stages, t, round_keys(seed), acc, md, ctrl);
   return cudaGetLastError();
 }
@@ -679,6 +604,10 @@ cudaError_t plaunch_mode(const uint32_t *src, uint32_t *dst, int L, uint32_t t, 
   if (wpt == 8) {
     if (fuse == 2) return plaunch<8, 2, MODE>(src, dst, L, t, seed, acc, md, ctrl, st);
     return plaunch<8, 1, MODE>(src, dst, L, t, seed, acc, md, ctrl, st);
+  }
+  if (L / 128 <= 256) {  // rows of at most 256 threads
+    if (fuse == 2) return plaunch<4, 2, MODE, true>(src, dst, L, t, seed, acc, md, ctrl, st);
+    return plaunch<4, 1, MODE, true>(src, dst, L, t, seed, acc, md, ctrl, st);
   }
   if (fuse == 2) return plaunch<4, 2, MODE>(src, dst, L, t, seed, acc, md, ctrl, st);
   return plaunch<4, 1, MODE>(src, dst, L, t, seed, acc, md, ctrl, st);

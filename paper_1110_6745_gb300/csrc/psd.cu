@@ -119,7 +119,7 @@ __device__ void scan_counts(const uint32_t *__restrict__ cnt, int64_t L, long lo
 // emptied every 15 rows), nY per row through a warp sum and shared-memory
 // row counters, added to cntY once per block.
 template <bool PAR>
-__global__ void __launch_bounds__(kCountThreads)
+__global__ void __launch_bounds__(kCountThreads, 3)
 profile_count_kernel(const uint32_t *__restrict__ P, int64_t L, int64_t R,
                      uint32_t *__restrict__ cntX, uint32_t *__restrict__ cntY) {
   __shared__ uint32_t rowacc[kBandMax];
@@ -140,33 +140,53 @@ profile_count_kernel(const uint32_t *__restrict__ P, int64_t L, int64_t R,
   int fill = 0;
   const int64_t wn = (w + 1 == W) ? 0 : w + 1;
   uint32_t cur = (PAR && on) ? P[ya * W + w] : 0u;
-  for (int64_t y = ya; y < yb; ++y) {
-    uint32_t xw = 0, yw = 0;
-    if (on) {
-      if (PAR) {
-        const int64_t yu = (y == L - 1) ? 0 : y + 1;
-        const uint32_t nx = P[y * W + wn], up = P[yu * W + w];
-        const uint32_t odd = odd_sites(y);
-        xw = ~(cur ^ __funnelshift_r(cur, nx, 1) ^ odd);
-        yw = ~(cur ^ up ^ odd);
-        cur = up;
-      } else {
-        xw = P[y * W + w];
-        yw = P[L * W + y * W + w];
+  // eight rows per batch: their loads are issued together (memory-level
+  // parallelism), then the rows are counted in order
+  for (int64_t y = ya; y < yb; y += 8) {
+    uint32_t la[8], lb[8];  // parity: row y+k+1 and word w+1 of row y+k; slopes: X, Y words
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int64_t yk = y + k;
+      la[k] = lb[k] = 0u;
+      if (on && yk < yb) {
+        if (PAR) {
+          const int64_t yu = (yk + 1 == L) ? 0 : yk + 1;
+          la[k] = P[yu * W + w];
+          lb[k] = P[yk * W + wn];
+        } else {
+          la[k] = P[yk * W + w];
+          lb[k] = P[L * W + yk * W + w];
+        }
       }
     }
 #pragma unroll
-    for (int j = 0; j < 4; ++j) A[j] += (xw >> j) & 0x11111111u;
-    if (++fill == 15) {
+    for (int k = 0; k < 8; ++k) {
+      if (y + k >= yb) break;  // the same for the whole block
+      uint32_t xw = 0, yw = 0;
+      if (on) {
+        if (PAR) {
+          const uint32_t odd = odd_sites(y + k);
+          xw = ~(cur ^ __funnelshift_r(cur, lb[k], 1) ^ odd);
+          yw = ~(cur ^ la[k] ^ odd);
+          cur = la[k];
+        } else {
+          xw = la[k];
+          yw = lb[k];
+        }
+      }
 #pragma unroll
-      for (int i = 0; i < 8; ++i)
+      for (int j = 0; j < 4; ++j) A[j] += (xw >> j) & 0x11111111u;
+      if (++fill == 15) {
 #pragma unroll
-        for (int j = 0; j < 4; ++j) cnt[4 * i + j] += (A[j] >> (4 * i)) & 15u;
-      A[0] = A[1] = A[2] = A[3] = 0;
-      fill = 0;
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) cnt[4 * i + j] += (A[j] >> (4 * i)) & 15u;
+        A[0] = A[1] = A[2] = A[3] = 0;
+        fill = 0;
+      }
+      const uint32_t n = __reduce_add_sync(0xFFFFFFFFu, (uint32_t)__popc(yw));
+      if ((tid & 31) == 0 && n) atomicAdd(&rowacc[y + k - ya], n);
     }
-    const uint32_t n = __reduce_add_sync(0xFFFFFFFFu, (uint32_t)__popc(yw));
-    if ((tid & 31) == 0 && n) atomicAdd(&rowacc[y - ya], n);
   }
 #pragma unroll
   for (int i = 0; i < 8; ++i)

@@ -13,7 +13,9 @@ requests that arrive while others run join at the next tick:
   budget and a stream is free. Its budget is enqueued in chunks of about
   `chunk_attempts` site updates, at most `ahead` chunks in flight, each
   closed by an event, so the stream never drains while the host loop runs
-  and the host never blocks on a full launch queue.
+  and the host never blocks on a full launch queue; its exact sums are
+  enqueued behind the last chunk (okz_moments_enqueue) and read once their
+  event has fired.
 
 The loop never waits on the device: the batched launch is also closed by an
 event and its slots are retired, and new small requests admitted, when that
@@ -73,8 +75,12 @@ class Server:
                  ahead=2, max_chunk_sweeps=256):
         import torch
         self._torch = torch
-        self.pool = okz.Batch(arena_bytes=small_arena_bytes, max_slots=max_slots)
-        self.pool_stream = torch.cuda.ExternalStream(self.pool.stream)
+        # the pool's stream has the higher priority: its short synchronous
+        # steps (admission, exact sums) then do not queue behind the large
+        # lattices' kernels
+        self.pool_stream = torch.cuda.Stream(priority=-1)
+        self.pool = okz.Batch(arena_bytes=small_arena_bytes, max_slots=max_slots,
+                              stream=self.pool_stream.cuda_stream)
         self.small_event = None
         self.max_slots = max_slots
         self.tick_sweeps = int(tick_sweeps)
@@ -148,17 +154,27 @@ class Server:
         return moved
 
     def _retire_large(self, t0):
-        done = [rid for rid, ent in self.large.items() if ent.remaining == 0 and not ent.inflight]
+        moved = False
+        # budget done: enqueue the exact sums behind the last chunk, close by an event
+        for ent in self.large.values():
+            if ent.remaining == 0 and not ent.inflight and ent.measured is None:
+                ent.sim.moments_enqueue()
+                ev = self._torch.cuda.Event()
+                ev.record(self.streams[ent.si])
+                ent.measured = ev
+                moved = True
+        done = [rid for rid, ent in self.large.items()
+                if ent.measured is not None and ent.measured.query()]
         for rid in done:
             ent = self.large.pop(rid)
-            Sk, W2, _, _ = ent.sim.moments()
+            Sk, W2, _, _ = ent.sim.moments_fetch()
             H0 = ent.sim.info().H0
             ent.sim.close()
             self.large_used -= ent.nbytes
             self.free_streams.append(ent.si)
             fin = time.perf_counter() - t0
             self.results[rid] = Result(rid, Sk, H0, W2, ent.admitted, fin, fin - ent.r.arrival)
-        return bool(done)
+        return moved or bool(done)
 
     # -- small lattices: one batched launch at a time -------------------------
     def _retire_small(self, t0):
@@ -229,6 +245,7 @@ class _Large:
     admitted: float
     nbytes: int
     chunk: int
+    measured: object = None  # event closing the enqueued exact sums
 
 
 def run_alone(r):

@@ -428,3 +428,18 @@ def test_random_sequential_growth_exponent(okz):
     b_rs, b_cb = beta(True), beta(False)
     assert 0.20 <= b_rs <= 0.28 and 0.20 <= b_cb <= 0.28, (b_rs, b_cb)
     assert abs(b_rs - b_cb) < 0.04, (b_rs, b_cb)
+
+
+def test_moments_enqueue_then_fetch(okz, orc):
+    """okz_moments_enqueue / okz_moments_fetch return what okz_moments returns
+    at the enqueue point, even with sweeps enqueued in between."""
+    ref = orc.Sim(480, 0.75, 0.25, 77)
+    ref.sweep(9)
+    with okz.Simulation(480, 0.75, 0.25, seed=77, kernel=okz.OKZ_KERNEL_PARITY_PLAIN) as sim:
+        sim.sweep(9)
+        direct = sim.moments()
+        sim.moments_enqueue()
+        sim.sweep(3)
+        assert sim.moments_fetch() == direct
+        assert direct[0] == ref.power_sums()
+        assert sim.moments() != direct  # the later sweeps are there
