@@ -28,8 +28,8 @@ constexpr int kCell = 32;
 constexpr int kCellStride = kCell + 3;  // rows 0..32, then the column x0+32; odd stride
 
 __global__ void __launch_bounds__(128)
-ddrs_kernel(uint32_t *__restrict__ B, int L, uint32_t t, const RoundKeys rk, uint64_t P32,
-            uint64_t Q32, Ctrl *__restrict__ ctrl) {
+ddrs_kernel(uint32_t *__restrict__ B, int L, uint32_t t, const RoundKeys rk, uint32_t Pm1,
+            uint32_t Qm1, uint32_t pq_on, Ctrl *__restrict__ ctrl) {
   __shared__ uint32_t cell_sm[128][kCellStride];
   uint32_t *cell = cell_sm[threadIdx.x];
   const int ncell = L / kCell;
@@ -48,6 +48,12 @@ ddrs_kernel(uint32_t *__restrict__ B, int L, uint32_t t, const RoundKeys rk, uin
     cell[ly] = __funnelshift_r(a, b, sh);
     if (ly < kCell) next_col |= ((b >> sh) & 1u) << ly;
   }
+  // loop invariants: p(x,y) = (x0 + lx + y0 + ly) mod 2 (L is even), and the
+  // local coordinates of site (0,0) if this cell holds it (else 64)
+  const uint32_t pbase = (uint32_t)(x0 + y0) & 1u;
+  const int lx00 = (L - x0) % L < kCell ? (L - x0) % L : 64;
+  const int ly00 = (L - y0) % L < kCell ? (L - y0) % L : 64;
+  const bool p_on = pq_on & 1u, q_on = pq_on & 2u;
   uint32_t touched = 0;
   int dH0 = 0;
   uint32_t r2 = 0, r3 = 0;
@@ -65,19 +71,21 @@ ddrs_kernel(uint32_t *__restrict__ B, int L, uint32_t t, const RoundKeys rk, uin
     }
     const int lx = (int)(first & (kCell - 1)), ly = (int)((first >> 16) & (kCell - 1));
     if (lx == 0 || ly == 0) continue;  // dead border
-    const int x = (x0 + lx) % L, y = (y0 + ly) % L;
     const uint32_t row = cell[ly];
-    const uint32_t cc = ((row >> lx) ^ (uint32_t)(x + y)) & 1u;  // own bit ^ parity
-    const uint32_t l = (row >> (lx - 1)) & 1u;
-    const uint32_t r = (lx == kCell - 1) ? (next_col >> ly) & 1u : (row >> (lx + 1)) & 1u;
+    // bits 0, 1, 2 = left neighbour, own site, right neighbour
+    const uint32_t hi = (next_col >> ly) & 1u;
+    const uint32_t w3 = __funnelshift_r(row, hi, lx - 1);
+    const uint32_t cc = ((w3 >> 1) ^ (uint32_t)(lx + ly) ^ pbase) & 1u;  // own bit ^ parity
     const uint32_t dn = (cell[ly - 1] >> lx) & 1u, up = (cell[ly + 1] >> lx) & 1u;
-    const bool is_min = l == cc && r == cc && dn == cc && up == cc;
-    const bool is_max = l != cc && r != cc && dn != cc && up != cc;
-    const bool accept = (is_min && (uint64_t)u < P32) || (is_max && (uint64_t)u < Q32);
+    const uint32_t s4 = (w3 & 1u) + ((w3 >> 2) & 1u) + dn + up;  // neighbours with bit 1
+    // a minimum has all four neighbours equal to cc, a maximum all four unequal
+    const bool all1 = s4 == 4u, all0 = s4 == 0u;
+    const bool is_min = cc ? all1 : all0, is_max = cc ? all0 : all1;
+    const bool accept = (is_min && p_on && u <= Pm1) || (is_max && q_on && u <= Qm1);
     if (!accept) continue;
     cell[ly] = row ^ (1u << lx);
     touched |= 1u << ly;
-    if (x == 0 && y == 0) dH0 += is_min ? 2 : -2;
+    if (lx == lx00 && ly == ly00) dH0 += is_min ? 2 : -2;
   }
   while (touched) {
     const int ly = __ffs(touched) - 1;
@@ -94,9 +102,12 @@ ddrs_kernel(uint32_t *__restrict__ B, int L, uint32_t t, const RoundKeys rk, uin
 
 cudaError_t launch_ddrs(uint32_t *B, int64_t L, uint32_t t, uint64_t seed, uint64_t P32,
                         uint64_t Q32, Ctrl *ctrl, cudaStream_t st) {
+  // u < P32 with P32 in [0, 2^32] as u <= P32 - 1 in 32 bits, P32 = 0 never
+  const uint32_t Pm1 = P32 ? (uint32_t)(P32 - 1) : 0u, Qm1 = Q32 ? (uint32_t)(Q32 - 1) : 0u;
+  const uint32_t pq_on = (P32 ? 1u : 0u) | (Q32 ? 2u : 0u);
   const int64_t cells = (L / kCell) * (L / kCell);
   ddrs_kernel<<<(unsigned)((cells + 127) / 128), 128, 0, st>>>(B, (int)L, t, round_keys(seed),
-                                                              P32, Q32, ctrl);
+                                                              Pm1, Qm1, pq_on, ctrl);
   return cudaGetLastError();
 }
 

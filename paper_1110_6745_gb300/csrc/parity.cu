@@ -110,118 +110,6 @@ cudaError_t launch_parity_halfsweep(uint32_t *B, int64_t L, int s, uint32_t t, u
 }
 
 // ---------------------------------------------------------------------------
-// Boundary conversions.
-// ---------------------------------------------------------------------------
-__global__ void to_slopes_kernel(const uint32_t *__restrict__ B, int64_t L,
-                                 uint32_t *__restrict__ out) {
-  const int64_t W = L >> 5, words = L * W;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < words;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t y = i / W, w = i - y * W;
-    const int64_t wr = (w == W - 1) ? 0 : w + 1, yu = (y == L - 1) ? 0 : y + 1;
-    const uint32_t c = B[i];
-    const uint32_t r = __funnelshift_r(c, B[y * W + wr], 1);
-    const uint32_t P = odd_mask(y);
-    out[i] = ~(c ^ r ^ P);               // sigma_x = +1 where b(x+1) ^ b ^ p == 0
-    out[words + i] = ~(c ^ B[yu * W + w] ^ P);  // sigma_y
-  }
-}
-
-cudaError_t launch_to_slopes(const uint32_t *B, int64_t L, uint32_t *out, cudaStream_t st) {
-  const int64_t words = L * (L >> 5);
-  int64_t blocks = (words + 255) / 256;
-  if (blocks > 152 * 64) blocks = 152 * 64;
-  to_slopes_kernel<<<(unsigned)blocks, 256, 0, st>>>(B, L, out);
-  return cudaGetLastError();
-}
-
-// b(0,y): b(0,0) = (H0/2) mod 2, b(0,y+1) = b(0,y) ^ p(0,y) ^ !sigma_y-bit(0,y).
-// One block; each thread a run of rows; block-wide exclusive xor-scan.
-__global__ void __launch_bounds__(1024)
-from_slopes_col_kernel(const uint32_t *__restrict__ slopes, int64_t L, long long H0,
-                       int64_t *__restrict__ bcol) {
-  __shared__ uint32_t warp_x[32];
-  const int64_t W = L >> 5;
-  const uint32_t *Yp = slopes + L * W;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int64_t R = (L + blockDim.x - 1) / blockDim.x;
-  const int64_t y0 = tid * R < L ? tid * R : L;
-  const int64_t y1 = y0 + R < L ? y0 + R : L;
-  uint32_t run = 0;
-  for (int64_t y = y0; y < y1; ++y) run ^= ((uint32_t)y & 1u) ^ (~Yp[y * W] & 1u);
-  uint32_t inc = run;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t n = __shfl_up_sync(0xFFFFFFFFu, inc, o);
-    if (lane >= o) inc ^= n;
-  }
-  if (lane == 31) warp_x[warp] = inc;
-  __syncthreads();
-  if (warp == 0) {
-    const int nw = blockDim.x >> 5;
-    uint32_t v = lane < nw ? warp_x[lane] : 0u, iv = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t n = __shfl_up_sync(0xFFFFFFFFu, iv, o);
-      if (lane >= o) iv ^= n;
-    }
-    if (lane < nw) warp_x[lane] = iv ^ v;  // exclusive
-  }
-  __syncthreads();
-  uint32_t b = (uint32_t)((H0 >> 1) & 1) ^ warp_x[warp] ^ inc ^ run;
-  for (int64_t y = y0; y < y1; ++y) {
-    bcol[y] = b;
-    b ^= ((uint32_t)y & 1u) ^ (~Yp[y * W] & 1u);
-  }
-}
-
-// Rows: b(x+1,y) = b(x,y) ^ p(x,y) ^ !sigma_x-bit(x,y). A warp per row, each
-// lane a run of words; in-word exclusive prefix xor, warp xor-scan of carries.
-__global__ void __launch_bounds__(256)
-from_slopes_row_kernel(const uint32_t *__restrict__ slopes, int64_t L,
-                       const int64_t *__restrict__ bcol, uint32_t *__restrict__ B) {
-  const int lane = threadIdx.x & 31;
-  const int64_t W = L >> 5;
-  const int64_t wpl = (W + 31) >> 5;
-  const int64_t w0 = lane * wpl < W ? lane * wpl : W;
-  const int64_t w1 = w0 + wpl < W ? w0 + wpl : W;
-  const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t y = gwarp; y < L; y += nwarps) {
-    const uint32_t P = odd_mask(y);
-    uint32_t par = 0;
-    for (int64_t w = w0; w < w1; ++w) par ^= __popc(P ^ ~slopes[y * W + w]) & 1u;
-    uint32_t inc = par;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t n = __shfl_up_sync(0xFFFFFFFFu, inc, o);
-      if (lane >= o) inc ^= n;
-    }
-    uint32_t carry = (uint32_t)bcol[y] ^ inc ^ par;  // b at my first site
-    for (int64_t w = w0; w < w1; ++w) {
-      const uint32_t d = P ^ ~slopes[y * W + w];  // bit x: b(x+1) ^ b(x)
-      uint32_t e = d;                             // inclusive prefix xor
-      e ^= e << 1;
-      e ^= e << 2;
-      e ^= e << 4;
-      e ^= e << 8;
-      e ^= e << 16;
-      B[y * W + w] = (e ^ d) ^ (carry ? ~0u : 0u);  // exclusive prefix ^ carry
-      carry ^= __popc(d) & 1u;
-    }
-  }
-}
-
-cudaError_t launch_from_slopes(const uint32_t *slopes, int64_t L, long long H0, int64_t *bcol,
-                               uint32_t *B, cudaStream_t st) {
-  from_slopes_col_kernel<<<1, 1024, 0, st>>>(slopes, L, H0, bcol);
-  int64_t nb = (L + 7) / 8;
-  if (nb > 152 * 16) nb = 152 * 16;
-  from_slopes_row_kernel<<<(unsigned)nb, 256, 0, st>>>(slopes, L, bcol, B);
-  return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------------------
 // Streaming kernel: F sweeps (2F half-sweep "stages") per launch; a CTA spans
 // full rows (L/(32*WPT) threads, WPT words each) and owns a band [yb, ye).
 // Stream row r (one 1-D TMA copy into a ring slot) drives a wavefront:

@@ -115,21 +115,42 @@ __device__ void scan_counts(const uint32_t *__restrict__ cnt, int64_t L, long lo
 }  // namespace
 
 // One thread per word column w and band of rows [ya, yb): nX per column
-// through nibble counters (bit 4i + j of the X words in nibble i of A[j],
-// emptied every 15 rows), nY per row through a warp sum and shared-memory
-// row counters, added to cntY once per block.
+// through nibble counters (bit 4i + j of the X words in nibble i of A[j]),
+// nY per row through a warp sum and shared-memory row counters, added to
+// cntY once per block. Rows go in batches of 15 (the nibble counters' range):
+// the batch's loads are issued together, then its rows are counted and the
+// nibbles emptied once; the few remaining rows (and the lattice's last row,
+// whose upper neighbour wraps to row 0) take a one-row path.
+template <bool PAR>
+__device__ __forceinline__ void count_row(uint32_t xw, uint32_t yw, uint32_t A[4],
+                                          uint32_t *rowacc_r, int lane) {
+#pragma unroll
+  for (int j = 0; j < 4; ++j) A[j] += (xw >> j) & 0x11111111u;
+  const uint32_t n = __reduce_add_sync(0xFFFFFFFFu, (uint32_t)__popc(yw));
+  if (lane == 0 && n) atomicAdd(rowacc_r, n);
+}
+
+__device__ __forceinline__ void empty_nibbles(uint32_t A[4], uint32_t cnt[32]) {
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) cnt[4 * i + j] += (A[j] >> (4 * i)) & 15u;
+  A[0] = A[1] = A[2] = A[3] = 0;
+}
+
 template <bool PAR>
 __global__ void __launch_bounds__(kCountThreads, 3)
-profile_count_kernel(const uint32_t *__restrict__ P, int64_t L, int64_t R,
+profile_count_kernel(const uint32_t *__restrict__ P, int64_t L64, int64_t R,
                      uint32_t *__restrict__ cntX, uint32_t *__restrict__ cntY) {
+  constexpr int kBatch = 15;
   __shared__ uint32_t rowacc[kBandMax];
-  const int64_t W = L >> 5;
-  const int tid = threadIdx.x;
-  const int64_t w = (int64_t)blockIdx.x * kCountThreads + tid;
+  const int L = (int)L64, W = L >> 5;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int w = (int)blockIdx.x * kCountThreads + tid;
   const bool on = w < W;
-  const int64_t ya = (int64_t)blockIdx.y * R;
-  const int64_t yb = ya + R < L ? ya + R : L;
-  const int nrow = (int)(yb - ya);
+  const int ya = (int)blockIdx.y * (int)R;
+  const int yb = ya + (int)R < L ? ya + (int)R : L;
+  const int nrow = yb - ya;
   for (int r = tid; r < nrow; r += kCountThreads) rowacc[r] = 0;
   __syncthreads();
 
@@ -137,61 +158,63 @@ profile_count_kernel(const uint32_t *__restrict__ P, int64_t L, int64_t R,
 #pragma unroll
   for (int b = 0; b < 32; ++b) cnt[b] = 0;
   uint32_t A[4] = {0, 0, 0, 0};
-  int fill = 0;
-  const int64_t wn = (w + 1 == W) ? 0 : w + 1;
-  uint32_t cur = (PAR && on) ? P[ya * W + w] : 0u;
-  // eight rows per batch: their loads are issued together (memory-level
-  // parallelism), then the rows are counted in order
-  for (int64_t y = ya; y < yb; y += 8) {
-    uint32_t la[8], lb[8];  // parity: row y+k+1 and word w+1 of row y+k; slopes: X, Y words
+  const int wc = on ? w : 0;                         // loads of idle lanes stay in bounds
+  const int dn_off = (wc + 1 == W) ? 1 - W : 1;      // word w+1, periodic in x
+  const size_t plane = (size_t)L * (size_t)W;
+  const uint32_t *pw = P + (size_t)ya * W + wc;      // row y, word w
+  uint32_t cur = PAR ? pw[0] : 0u;
+  // rows whose upper neighbour does not wrap
+  const int ymain = (PAR && yb == L) ? yb - 1 : yb;
+  int y = ya;
+  for (; y + kBatch <= ymain; y += kBatch, pw += (size_t)kBatch * W) {
+    uint32_t la[kBatch], lb[kBatch];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const int64_t yk = y + k;
-      la[k] = lb[k] = 0u;
-      if (on && yk < yb) {
-        if (PAR) {
-          const int64_t yu = (yk + 1 == L) ? 0 : yk + 1;
-          la[k] = P[yu * W + w];
-          lb[k] = P[yk * W + wn];
-        } else {
-          la[k] = P[yk * W + w];
-          lb[k] = P[L * W + yk * W + w];
-        }
+    for (int k = 0; k < kBatch; ++k) {
+      if (PAR) {
+        la[k] = pw[(k + 1) * W];       // b of row y+k+1
+        lb[k] = pw[k * W + dn_off];    // b of word w+1, row y+k
+      } else {
+        la[k] = pw[k * W];             // X word
+        lb[k] = pw[plane + k * W];     // Y word
       }
     }
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      if (y + k >= yb) break;  // the same for the whole block
-      uint32_t xw = 0, yw = 0;
-      if (on) {
-        if (PAR) {
-          const uint32_t odd = odd_sites(y + k);
-          xw = ~(cur ^ __funnelshift_r(cur, lb[k], 1) ^ odd);
-          yw = ~(cur ^ la[k] ^ odd);
-          cur = la[k];
-        } else {
-          xw = la[k];
-          yw = lb[k];
-        }
+    for (int k = 0; k < kBatch; ++k) {
+      uint32_t xw, yw;
+      if (PAR) {
+        const uint32_t odd = odd_sites(y + k);
+        xw = ~(cur ^ __funnelshift_r(cur, lb[k], 1) ^ odd);
+        yw = ~(cur ^ la[k] ^ odd);
+        cur = la[k];
+      } else {
+        xw = la[k];
+        yw = lb[k];
       }
-#pragma unroll
-      for (int j = 0; j < 4; ++j) A[j] += (xw >> j) & 0x11111111u;
-      if (++fill == 15) {
-#pragma unroll
-        for (int i = 0; i < 8; ++i)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) cnt[4 * i + j] += (A[j] >> (4 * i)) & 15u;
-        A[0] = A[1] = A[2] = A[3] = 0;
-        fill = 0;
-      }
-      const uint32_t n = __reduce_add_sync(0xFFFFFFFFu, (uint32_t)__popc(yw));
-      if ((tid & 31) == 0 && n) atomicAdd(&rowacc[y + k - ya], n);
+      if (!on) xw = yw = 0u;
+      count_row<PAR>(xw, yw, A, &rowacc[y + k - ya], lane);
+    }
+    empty_nibbles(A, cnt);
+  }
+  for (int k = 0; y < yb; ++y, ++k, pw += W) {  // fewer than kBatch rows, or the wrapping row
+    uint32_t xw, yw;
+    if (PAR) {
+      const uint32_t up = (y + 1 == L) ? P[wc] : pw[W];
+      const uint32_t odd = odd_sites(y);
+      xw = ~(cur ^ __funnelshift_r(cur, pw[dn_off], 1) ^ odd);
+      yw = ~(cur ^ up ^ odd);
+      cur = up;
+    } else {
+      xw = pw[0];
+      yw = pw[plane];
+    }
+    if (!on) xw = yw = 0u;
+    count_row<PAR>(xw, yw, A, &rowacc[y - ya], lane);
+    if (k == kBatch - 1) {
+      empty_nibbles(A, cnt);
+      k = -1;
     }
   }
-#pragma unroll
-  for (int i = 0; i < 8; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) cnt[4 * i + j] += (A[j] >> (4 * i)) & 15u;
+  empty_nibbles(A, cnt);
   __syncthreads();
   for (int r = tid; r < nrow; r += kCountThreads)
     if (rowacc[r]) atomicAdd(&cntY[ya + r], rowacc[r]);
