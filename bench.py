@@ -45,17 +45,33 @@ ALU_OPS_PER_SITE_SWEEP = {"parity": 2 * 7 / 32 + 20 / 128,
 ALU_LANES_PER_SM = 64  # INT32 ALU-pipe lanes per SM per clock (16 per sub-partition)
 N_SMS = 152
 
-# dram__bytes_read.sum + dram__bytes_write.sum of one sweep-kernel launch (ncu,
-# L = 65536, 2 sweeps per launch), per site; valid only for the kernel source
-# with this SHA-256 (traffic is reported as null once the source changes).
-TRAFFIC_BYTES_PER_SITE = {"parity": (556870144 + 489893376) / 65536 ** 2}
-TRAFFIC_SOURCE_SHA = {"parity": "7f35d7429097d45ac0a1bef97cb8320a9de4e0088da9bf5999553a3571834f33"}
-KERNEL_SOURCE = {"parity": "parity.cu", "slope": "sweep_stream.cu"}
+# dram__bytes_read.sum + dram__bytes_write.sum per site of one launch of each
+# dominant kernel (ncu on a small case, profiles/ gives the commands), valid
+# only for the kernel source with the recorded SHA-256: traffic is reported as
+# null once the source changes.
+#   parity_stream_kernel  L = 65536, one launch = 2 sweeps
+#   ddrs_kernel           L = 32768, one launch = 1 sweep
+#   profile_count_kernel  L = 65536, one profile pass
+TRAFFIC = {
+    "parity": ((556867840 + 486643200) / 65536 ** 2, "parity.cu",
+               "681ae3de647d0e22ef1eb6869aeacf87aaa5d73ff27da7c0531b5dd271c83f6e"),
+    "ddrs": ((134345472 + 73289472) / 32768 ** 2, "ddrs.cu",
+             "6b2f2cbd191834694811fdbf474fc5eb0e73a9edebfc66c6b7baab2356f97324"),
+    "profile": ((538082560 + 15609600) / 65536 ** 2, "psd.cu",
+                "e006ee1ddc9f3670b621c81c5870b40ffd0229b3359201d9da06bd46e8d03c8a"),
+}
 
 
-def _kernel_sha(repr_name):
-    p = os.path.join(ROOT, "paper_1110_6745_gb300", "csrc", KERNEL_SOURCE[repr_name])
-    return hashlib.sha256(open(p, "rb").read()).hexdigest()
+def _traffic(name, sites):
+    """Measured DRAM bytes of one launch of kernel `name` over `sites` sites,
+    or None if its source has changed since the measurement."""
+    if name not in TRAFFIC:
+        return None
+    per_site, src, sha = TRAFFIC[name]
+    path = os.path.join(ROOT, "paper_1110_6745_gb300", "csrc", src)
+    if hashlib.sha256(open(path, "rb").read()).hexdigest() != sha:
+        return None
+    return per_site * sites
 
 
 def _peaks():
@@ -260,10 +276,7 @@ def run_gpu(args, world, rank, local):
     alg_bytes = BYTES_PER_SITE_LAUNCH[repr_name] * N
     achieved = alg_bytes / per_launch_s / 1e9
     peak, peak_kind = _peaks()
-    traffic = None
-    if (repr_name in TRAFFIC_BYTES_PER_SITE
-            and TRAFFIC_SOURCE_SHA.get(repr_name) == _kernel_sha(repr_name)):
-        traffic = TRAFFIC_BYTES_PER_SITE[repr_name] * N
+    traffic = _traffic(repr_name, N) if fuse == 2 else None  # measured at 2 sweeps/launch
     # ALU roof: algorithmic ALU-pipe ops per launch / launch time, against
     # 152 SMs x 64 lanes x the SM clock sampled during the timed region
     sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
@@ -493,7 +506,7 @@ def run_rs(args, world, rank, local):
                    "l2": "inputs larger than L2 (2 GiB parity plane)"},
         "roofline": {"bound": "alu", "achieved": alu_ops / launch_s / 1e12, "peak": alu_peak,
                      "unit": "Tops/s", "frac": alu_ops / launch_s / 1e12 / alu_peak,
-                     "traffic": None, "kernel": "ddrs_kernel",
+                     "traffic": _traffic("ddrs", N), "kernel": "ddrs_kernel",
                      "peak_kind": "derived: 152 SMs x 64 INT32 lanes x sampled SM clock",
                      "ops_per_launch": alu_ops, "launch_ms": launch_s * 1e3},
         "gpu_launches": steps * (per_step + 3),
@@ -551,7 +564,8 @@ def run_spectrum(args, world, rank, local):
                                "device-to-host copies included", "L": L,
                    "l2": "inputs larger than L2 (2 GiB parity plane)"},
         "roofline": {"bound": "hbm", "achieved": alg / gpu_s / 1e9, "peak": peak,
-                     "unit": "GB/s", "frac": alg / gpu_s / 1e9 / peak, "traffic": None,
+                     "unit": "GB/s", "frac": alg / gpu_s / 1e9 / peak,
+                     "traffic": _traffic("profile", N),
                      "kernel": "profile_count_kernel (+ scan and FFT, all in the interval)",
                      "bytes_per_call": alg, "gpu_ms_per_call": gpu_s * 1e3,
                      "peak_kind": peak_kind},

@@ -236,7 +236,7 @@ band_sum_kernel(uint32_t *__restrict__ cntX, int64_t L, int64_t nb) {
   cntX[x] = s;
 }
 
-// col[0], row[0], then the two scans (one block).
+// col[0] and the column scan (block 0), row[0] and the row scan (block 1).
 template <bool PAR>
 __global__ void __launch_bounds__(1024)
 profile_finish_kernel(const uint32_t *__restrict__ P, int64_t L,
@@ -245,19 +245,21 @@ profile_finish_kernel(const uint32_t *__restrict__ P, int64_t L,
                       int64_t *__restrict__ row) {
   __shared__ long long sh[32];
   const int64_t W = L >> 5;
-  long long s0 = 0, s1 = 0;
-  for (int64_t y = threadIdx.x; y < L; y += blockDim.x) s0 += hcol[y];
-  for (int64_t w = threadIdx.x; w < W; w += blockDim.x) {
-    const uint32_t v = x_word<PAR>(P, W, w, 0);
-    for (int b = 0; b < 32; ++b) {
-      const long long wgt = L - 1 - (32 * w + b);
-      s1 += ((v >> b) & 1u) ? wgt : -wgt;
+  if (blockIdx.x == 0) {  // columns: col[0] = sum_y (h(0,y) - H0), then the scan
+    long long s0 = 0;
+    for (int64_t y = threadIdx.x; y < L; y += blockDim.x) s0 += hcol[y];
+    scan_counts(cntX, L, block_sum(s0, sh), col, sh);
+  } else {  // rows: row[0] = sum_x (L-1-x) sigma_x(x,0), then the scan
+    long long s1 = 0;
+    for (int64_t w = threadIdx.x; w < W; w += blockDim.x) {
+      const uint32_t v = x_word<PAR>(P, W, w, 0);
+      for (int b = 0; b < 32; ++b) {
+        const long long wgt = L - 1 - (32 * w + b);
+        s1 += ((v >> b) & 1u) ? wgt : -wgt;
+      }
     }
+    scan_counts(cntY, L, block_sum(s1, sh), row, sh);
   }
-  const long long col0 = block_sum(s0, sh);
-  const long long row0 = block_sum(s1, sh);
-  scan_counts(cntX, L, col0, col, sh);
-  scan_counts(cntY, L, row0, row, sh);
 }
 
 // a[t][bitrev(i)] = (t ? row : col)[i], the input of an in-place radix-2 FFT.
@@ -325,9 +327,9 @@ cudaError_t launch_profiles(const uint32_t *planes, int64_t L, bool parity, int6
     profile_count_kernel<false><<<grid, kCountThreads, 0, st>>>(planes, L, bp.R, cntX, cntY);
   band_sum_kernel<<<(unsigned)((L + 255) / 256), 256, 0, st>>>(cntX, L, bp.nb);
   if (parity)
-    profile_finish_kernel<true><<<1, 1024, 0, st>>>(planes, L, hcol, cntX, cntY, col, row);
+    profile_finish_kernel<true><<<2, 1024, 0, st>>>(planes, L, hcol, cntX, cntY, col, row);
   else
-    profile_finish_kernel<false><<<1, 1024, 0, st>>>(planes, L, hcol, cntX, cntY, col, row);
+    profile_finish_kernel<false><<<2, 1024, 0, st>>>(planes, L, hcol, cntX, cntY, col, row);
   return cudaGetLastError();
 }
 
