@@ -53,8 +53,8 @@ N_SMS = 152
 #   ddrs_kernel           L = 32768, one launch = 1 sweep
 #   profile_count_kernel  L = 65536, one profile pass
 TRAFFIC = {
-    "parity": ((556867840 + 486643200) / 65536 ** 2, "parity.cu",
-               "681ae3de647d0e22ef1eb6869aeacf87aaa5d73ff27da7c0531b5dd271c83f6e"),
+    "parity": ((557193984 + 486310400) / 65536 ** 2, "parity.cu",
+               "11fc9427ebed069d66adf0e1adf9573d4bd6a8e6c864578f603477cd081b1e83"),
     "ddrs": ((134345472 + 73289472) / 32768 ** 2, "ddrs.cu",
              "6b2f2cbd191834694811fdbf474fc5eb0e73a9edebfc66c6b7baab2356f97324"),
     "profile": ((538082560 + 15609600) / 65536 ** 2, "psd.cu",
@@ -576,6 +576,50 @@ def run_spectrum(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def run_steady(args, world, rank, local):
+    """--workload steady: the steady-state statistics of Secs. III-IV on the
+    batched kernels -- 304 replicas at each L = 64 .. 512 run from the striped
+    start for 4 L^1.61 sweeps and sampled 8 times L^1.61 sweeps apart (exact
+    W^2 per sample); alpha_eff (Eq. (13)) and kappa_2 / kappa_1^2 per L."""
+    import numpy as np
+    import torch
+
+    from paper_1110_6745_gb300.analysis import alpha_eff, steady_state_w2, w2_cumulants
+
+    torch.cuda.set_device(local)
+    Ls, R, nsamp = [64, 128, 256, 512], 304, 8
+    means, ratios, attempts = {}, {}, 0.0
+    _barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for L in Ls:
+        tx = L ** 1.61
+        burn, every = int(4 * tx), int(tx)
+        w = steady_state_w2(L, R, burn, nsamp, every, seed0=100000 + 1000 * L + 10 ** 6 * rank)
+        k = w2_cumulants(w)
+        means[L], ratios[L] = float(w.mean()), k[1] / k[0] ** 2
+        attempts += float(L) ** 2 * R * (burn + nsamp * every)
+    torch.cuda.synchronize()
+    dt = _max_over_ranks(world, time.perf_counter() - t0)
+    Le, ae = alpha_eff(Ls, [means[L] for L in Ls])
+    if rank != 0:
+        return
+    line = {
+        "metric": "aggregate site-update attempts/s, steady-state sampling", "unit": UNIT,
+        "value": world * attempts / dt / 1e9, "n_gpus": world, "steps": 1, "warmup": 0,
+        "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic", "impl": "okz-steady",
+        "config": {"workload": "steady state, 304 replicas per L in {64,128,256,512}, p=1 q=0 "
+                               "s_sel=1/2, 4 L^1.61 burn-in sweeps, 8 samples L^1.61 apart",
+                   "replicas": R, "samples": nsamp},
+        "w2_mean_by_L": {str(L): means[L] for L in Ls},
+        "alpha_eff": {str(int(L)): float(a) for L, a in zip(Le, ae)},
+        "kappa2_over_kappa1_sq": {str(L): float(ratios[L]) for L in Ls},
+        "paper_alpha": 0.393,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -588,7 +632,7 @@ def main():
     ap.add_argument("--wpt", type=int, default=0, help="words per thread (0 = library choice)")
     ap.add_argument("--fuse", type=int, default=0, help="sweeps per launch (0 = library choice)")
     ap.add_argument("--workload", default="growth",
-                    choices=["growth", "batched", "served", "rs", "spectrum"])
+                    choices=["growth", "batched", "served", "rs", "spectrum", "steady"])
     ap.add_argument("--budget-frac", type=int, default=64,
                     help="batched: run ceil(4 L^1.61)/frac sweeps per replica")
     ap.add_argument("--baseline-frac", type=int, default=2048,
@@ -606,6 +650,8 @@ def main():
         run_rs(args, world, rank, local)
     elif args.workload == "spectrum":
         run_spectrum(args, world, rank, local)
+    elif args.workload == "steady":
+        run_steady(args, world, rank, local)
     else:
         run_gpu(args, world, rank, local)
     if world > 1:

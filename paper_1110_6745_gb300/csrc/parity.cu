@@ -177,14 +177,29 @@ __device__ __forceinline__ void pstage(const uint32_t c[WPT], uint32_t lbit, uin
       eqq[j] = (acc.Q >= full || acc.Q == 0) ? 0u : mx[j];
       any |= eqp[j] | eqq[j];
     }
-    for (int m = 0; m < acc.k && any != 0u; ++m) {
+    if constexpr (KC > 1) {
+      // levels 0..KC-1: drawn once per sweep and carried between its stages
+      // (compile-time indices, so the cache stays in registers)
+#pragma unroll
+      for (int m = 0; m < KC; ++m) {
+        if (m >= acc.k || any == 0u) break;
+        const uint32_t pb = (uint32_t)(acc.P >> (acc.k - 1 - m)) & 1u;
+        const uint32_t qb = (uint32_t)(acc.Q >> (acc.k - 1 - m)) & 1u;
+        any = 0;
+#pragma unroll
+        for (int j = 0; j < WPT; ++j) {
+          lt_step(lv[m][j], pb, ltp[j], eqp[j]);
+          lt_step(lv[m][j], qb, ltq[j], eqq[j]);
+          any |= eqp[j] | eqq[j];
+        }
+      }
+    }
+    // level 0 from the cache when KC == 1; further levels drawn when needed
+    for (int m = (KC > 1 ? KC : 0); m < acc.k && any != 0u; ++m) {
       uint32_t rr[WPT];
-      if (m < KC) {  // levels drawn once per sweep and carried between its stages
+      if (KC == 1 && m == 0) {
 #pragma unroll
-        for (int mm = 0; mm < KC; ++mm)
-          if (mm == m)
-#pragma unroll
-            for (int j = 0; j < WPT; ++j) rr[j] = lv[mm][j];
+        for (int j = 0; j < WPT; ++j) rr[j] = lv[0][j];
       } else {
 #pragma unroll
         for (int gq = 0; gq < WPT / 4; ++gq) {
