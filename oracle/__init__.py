@@ -1,7 +1,7 @@
 """Plain CPU oracle of the octahedron-model sweep (Kelling & Odor, arXiv:1110.6745).
 
 TEST INFRASTRUCTURE. Only tests/, ``__graft_entry__.smoke()`` and bench.py's
-CPU-baseline leg may import this package. The product path (the CUDA library
+CPU legs (CPU baseline, reference arm) may import this package. The product path (the CUDA library
 under ``paper_1110_6745_gb300``) never imports it and shares no code with it.
 
 The arithmetic lives in ``okz_oracle.c``; this module only marshals numpy

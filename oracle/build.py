@@ -1,7 +1,7 @@
 """Compile the CPU oracle (plain C, gcc + OpenMP) into oracle/_build/liboracle.so.
 
 Test infrastructure: the library built here is loaded only by the test suite,
-the smoke check and the benchmark's CPU-baseline leg.
+the smoke check and the benchmark's CPU legs (CPU baseline, reference arm).
 """
 import os
 import subprocess

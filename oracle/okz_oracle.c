@@ -4,7 +4,8 @@
  * Kardar-Parisi-Zhang model using graphics cards" (arXiv:1110.6745).
  *
  * TEST INFRASTRUCTURE ONLY. The test suite, the smoke check and the
- * benchmark's CPU-baseline leg are the only code allowed to load this library.
+ * benchmark's CPU legs (its CPU baseline and its reference arm) are the only
+ * code allowed to load this library.
  * The CUDA library shares no code with it: no headers, no helpers, no tables.
  *
  * Everything here is written for a reader checking it against the paper by
