@@ -284,28 +284,43 @@ def run_gpu(args, world, rank, local):
     alu_ops = ALU_OPS_PER_SITE_SWEEP[repr_name] * N * fuse
     alu_achieved = alu_ops / per_launch_s / 1e12
 
-    # end to end through the C-ABI with host buffers: each step restores the
-    # lattice from pinned host memory, sweeps, and reads back the exact sums
+    # end to end through the C-ABI with host buffers: every step's input (the
+    # whole lattice state, 4 GiB) comes from pinned host memory and its exact
+    # sums go back to the host. Step k+1's input is copied on a copy stream
+    # while step k sweeps (two device staging buffers); all copies lie inside
+    # the timed region.
     e2e_steps = min(args.steps, 8)
     host_planes = torch.empty(2 * L * L // 32, dtype=torch.int32, pin_memory=True)
     host_planes.copy_(start_planes.cpu())
+    staging = [torch.empty_like(start_planes) for _ in range(2)]
+    copy_stream = torch.cuda.Stream(device=dev)
+    ready = [torch.cuda.Event() for _ in range(2)]
+
+    def prefetch(k):
+        with torch.cuda.stream(copy_stream):
+            staging[k % 2].copy_(host_planes, non_blocking=True)
+            ready[k % 2].record(copy_stream)
+
+    def e2e_step(k, last):
+        stream.wait_event(ready[k % 2])
+        sim.restore(staging[k % 2], 0, 0)  # device-to-device + conversion, synchronous
+        if not last:
+            prefetch(k + 1)
+        sim.sweep(SWEEPS_PER_STEP)
+        return sim.width2()
+
     # untimed warm-up of the end-to-end leg: the first DMA from a freshly
     # pinned buffer pays a one-time mapping cost
-    sim.restore(host_planes, 0, 0)
-    sim.sweep(SWEEPS_PER_STEP)
-    sim.width2()
+    prefetch(0)
+    e2e_step(0, True)
     torch.cuda.synchronize(dev)
     _barrier(world)
     e2e_clocks = ClockSampler(local)
     e2e_clocks.start()
     t0 = time.perf_counter()
-    restore_s = 0.0
-    for _ in range(e2e_steps):
-        ta = time.perf_counter()
-        sim.restore(host_planes, 0, 0)  # synchronous: H2D copy + conversion
-        restore_s += time.perf_counter() - ta
-        sim.sweep(SWEEPS_PER_STEP)
-        sim.width2()
+    prefetch(0)
+    for k in range(e2e_steps):
+        e2e_step(k, k + 1 == e2e_steps)
     torch.cuda.synchronize(dev)
     e2e_s = _max_over_ranks(world, time.perf_counter() - t0, dev)
     e2e_clk = e2e_clocks.stop()
@@ -343,8 +358,8 @@ def run_gpu(args, world, rank, local):
         "gpu_launches": launches,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": e2e_steps, "clocks": e2e_clk,
-                "restore_ms_per_step": restore_s / e2e_steps * 1e3,
-                "ms_per_step": e2e_s / e2e_steps * 1e3},
+                "ms_per_step": e2e_s / e2e_steps * 1e3,
+                "pipelining": "H2D of step k+1 on a copy stream during step k"},
         "w2_final": w2_final,
         "clocks": clk,
     }
