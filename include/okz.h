@@ -252,6 +252,17 @@ okz_status okz_destroy(okz_sim *sim);
 /* Message of the calling thread's most recent failure ("" if none). */
 const char *okz_last_error(void);
 
+/* okz_selftest_wait_timeout -- the paper has no counterpart to this entry
+ * point. Self-test of the bounded device-side wait the streaming kernels use
+ * for their TMA copies: one block arms an mbarrier for a 16-byte transaction
+ * that is never issued and waits on it with the library's wait limit (2 s
+ * of %globaltimer). Returns OKZ_ETIMEOUT when the bound works -- the kernel
+ * gives up, reports the timeout and exits, and the context stays usable --
+ * and OKZ_OK if the wait completed (a defect). stream is a cudaStream_t (NULL
+ * = the legacy default stream); synchronizing; uses 4 bytes of
+ * stream-ordered device memory. Errors: ENOMEM, ECUDA. */
+okz_status okz_selftest_wait_timeout(void *stream);
+
 /* okz_width2_noalloc -- the paper has no counterpart to this entry point; it
  * serves callers that cannot allocate device memory when they measure, e.g.
  * because a framework's caching allocator already holds all free device

@@ -70,6 +70,7 @@ _SIGS = {
     "okz_heights": (_c.c_int, [_vp, _c.c_int64, _c.c_int64, _vp, _c.c_int]),
     "okz_profiles": (_c.c_int, [_vp, _vp, _vp]),
     "okz_moments_enqueue": (_c.c_int, [_vp]),
+    "okz_selftest_wait_timeout": (_c.c_int, [_vp]),
     "okz_moments_fetch": (_c.c_int, [_vp, _c.POINTER(okz_i128), _c.POINTER(_c.c_double),
                                _c.POINTER(_c.c_double), _c.POINTER(_c.c_double)]),
     "okz_psd": (_c.c_int, [_vp, _vp]),
@@ -186,6 +187,12 @@ def okz_width2(h):
     _check(lib().okz_width2(h, ctypes.byref(S1), ctypes.byref(S2), ctypes.byref(W2)),
            "okz_width2")
     return S1.value(), S2.value(), W2.value
+
+
+def okz_selftest_wait_timeout(stream=None):
+    """Runs the bounded-wait self-test; raises OkzError(OKZ_ETIMEOUT) when the
+    wait gave up as intended, returns if it (wrongly) completed."""
+    _check(lib().okz_selftest_wait_timeout(stream), "okz_selftest_wait_timeout")
 
 
 def okz_moments_enqueue(h):

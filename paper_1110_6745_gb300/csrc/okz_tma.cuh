@@ -43,7 +43,7 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
   return ok != 0;
 }
 
-__device__ __noinline__ bool mbar_wait_slow(uint64_t *bar, uint32_t parity) {
+static __device__ __noinline__ bool mbar_wait_slow(uint64_t *bar, uint32_t parity) {
   const uint64_t start = globaltimer_ns();
   while (true) {
     for (int i = 0; i < 64; ++i)
