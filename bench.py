@@ -164,7 +164,7 @@ def _max_over_ranks(world, v, device=None):
     return float(t.item())
 
 
-def cpu_baseline(L=16384, sweeps=10):
+def cpu_baseline(L=16384, sweeps=40):
     """The CPU oracle as it stands on a bounded sample of the workload."""
     import oracle
     sim = oracle.Sim(L, 1.0, 0.0, SEED)
