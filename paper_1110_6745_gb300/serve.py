@@ -6,8 +6,10 @@ loop admits arrived requests whenever a slot and device memory are free, so
 requests that arrive while others run join at the next tick:
 
 * L <= 2048: a slot of an okz_batch pool (the arena is the HBM budget for
-  small lattices); every tick advances all active slots by up to
-  `tick_sweeps` sweeps in one graph-captured persistent launch;
+  small lattices); every tick advances all active slots in one
+  graph-captured persistent launch, each by about the site updates of
+  `tick_sweeps` sweeps of an L = 2048 lattice (so the tick's CTAs work about
+  equally long and small lattices finish in few ticks);
 * L >= 4096: a simulation of its own (parity-plane stream kernel) on its own
   CUDA stream, admitted while its okz_device_bytes fit in the large-lattice
   budget and a stream is free. Its budget is enqueued in chunks of about
@@ -72,7 +74,7 @@ def poisson_requests(n=10000, rate=200.0, seed=2027, log_budget=(2.0, 4.0), expo
 class Server:
     def __init__(self, small_arena_bytes=1 << 31, max_slots=1024, large_bytes=8 << 30,
                  max_large=16, tick_sweeps=128, large_threshold=4096, chunk_attempts=2e10,
-                 ahead=2, max_chunk_sweeps=256):
+                 ahead=2, max_chunk_sweeps=256, equal_ticks=True):
         import torch
         self._torch = torch
         # the pool's stream has the higher priority: its short synchronous
@@ -84,6 +86,11 @@ class Server:
         self.small_event = None
         self.max_slots = max_slots
         self.tick_sweeps = int(tick_sweeps)
+        # equal_ticks: every slot gets about the site updates of tick_sweeps
+        # sweeps of an L = 2048 lattice per tick, so a tick's CTAs work about
+        # equally long and small lattices finish in few ticks
+        self.equal_ticks = bool(equal_ticks)
+        self.tick_attempts = float(tick_sweeps) * 2048.0 ** 2
         self.large_threshold = int(large_threshold)
         self.large_bytes = int(large_bytes)
         self.large_used = 0
@@ -190,7 +197,9 @@ class Server:
     def _launch_small(self):
         sweeps = np.zeros(self.max_slots, np.int64)
         for slot, ent in self.small.items():
-            n = min(ent[1], self.tick_sweeps)
+            per_tick = (max(1, int(self.tick_attempts // (ent[0].L * ent[0].L)))
+                        if self.equal_ticks else self.tick_sweeps)
+            n = min(ent[1], per_tick)
             sweeps[slot] = n
             ent[1] -= n
             self.attempts += float(ent[0].L) ** 2 * n
@@ -287,7 +296,9 @@ def bench(args, world, rank, local, unit):
         "config": {"workload": "10^4 requests, Poisson 200/s (PCG64 2027), L = 2^e, "
                                "e ~ U{7..13}, p ~ U{1, 0.75, 0.5}, q = 1 - p, budgets "
                                "round(10^U(2,4)) sweeps, admitted by slot and HBM footprint",
-                   "requests": len(reqs), "tick_sweeps": srv.tick_sweeps},
+                   "requests": len(reqs), "tick_sweeps": srv.tick_sweeps,
+                   "tick": ("equal site updates per slot (tick_sweeps sweeps of L = 2048)"
+                            if srv.equal_ticks else "tick_sweeps sweeps per slot")},
         "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                       "max": float(lat.max())},
         "latency_by_L_s": {str(L): [float(np.percentile(lat[m], 50)),
