@@ -171,12 +171,14 @@ okz_status okz_create_ex(const okz_params *prm, void *dev_buf, size_t bytes, voi
   int wpt = prm->words_per_thread, fuse = prm->sweeps_per_pass;
   if (streamed) {
     // defaults measured on GB300. Slope planes: 8 words per thread where the
-    // row allows it, one sweep per pass. Parity plane: two sweeps per pass at
-    // every size, 8 words per thread from L = 16384 up (4 below: a CTA spans
-    // one short row, and 4 words per thread doubles its threads).
+    // row allows it, one sweep per pass. Parity plane: 8 words per thread
+    // from L = 16384 up (4 below: a CTA spans one short row, and 4 words per
+    // thread doubles its threads); two sweeps per pass with one random level
+    // per site (k = 1), one sweep per pass with k >= 2 (the fused general-k
+    // kernels hold too many registers: one pass per sweep is 8-30 % faster)
     if (kernel == OKZ_KERNEL_PARITY_STREAM) {
       if (wpt == 0) wpt = (prm->L >= 16384 && stream_wpt_valid(prm->L, 8)) ? 8 : 4;
-      if (fuse == 0) fuse = 2;
+      if (fuse == 0) fuse = (k >= 2) ? 1 : 2;
     } else {
       if (wpt == 0) wpt = stream_wpt_valid(prm->L, 8) ? 8 : 4;
       if (fuse == 0) fuse = 1;
