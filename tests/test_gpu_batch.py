@@ -123,3 +123,36 @@ def test_replica_mix_matches_single_runs(okz):
         for j, r in enumerate(pick):
             planes, H0, t, Sk, w2, *_ = _single(okz, Ls[j], 0.95, 0.05, 1000 + int(r), sweeps[j])
             assert np.array_equal(b.state(j)[0], planes) and W2[j] == w2, (j, Ls[j])
+
+
+def test_full_replica_mix_against_single_runs_and_oracle(okz, orc):
+    """All 4096 replicas of the batched workload's mix (budgets
+    ceil(4 L^1.61) / 4096 sweeps) in one batch: every replica's exact sums
+    S1..S4 and H0 equal a run of its own with the in-place parity kernel, and
+    a 66-replica subset (11 of each size L = 64 .. 2048) equals the CPU
+    oracle bit for bit."""
+    rng = np.random.Generator(np.random.PCG64(2026))
+    e = rng.integers(6, 12, size=4096)
+    L = (1 << e).astype(np.int64)
+    T = np.ceil(4 * L.astype(np.float64) ** 1.61).astype(np.int64)
+    sweeps = np.maximum(1, T // 4096)
+    n = len(L)
+    with okz.Batch([int(x) for x in L], [0.95] * n, [0.05] * n,
+                   [1000 + r for r in range(n)]) as b:
+        b.run(sweeps)
+        got = b.measure(range(n))
+    for r in range(n):
+        Sk, H0, t = got[r]
+        with okz.Simulation(int(L[r]), 0.95, 0.05, seed=1000 + r,
+                            kernel=okz.OKZ_KERNEL_PARITY_PLAIN) as sim:
+            sim.sweep(int(sweeps[r]))
+            ref_Sk, _, _, _ = sim.moments()
+            assert (Sk, H0, t) == (ref_Sk, sim.info().H0, int(sweeps[r])), r
+    subset = []
+    for size in range(6, 12):
+        subset += [int(r) for r in np.nonzero(e == size)[0][:11]]
+    for r in subset:
+        ref = orc.Sim(int(L[r]), 0.95, 0.05, 1000 + r)
+        ref.sweep(int(sweeps[r]))
+        Sk, H0, t = got[r]
+        assert Sk == ref.power_sums() and H0 == ref.H0 and t == ref.t, r
