@@ -179,6 +179,20 @@ def cpu_baseline(L=16384, sweeps=40):
                                                                      L * L * sweeps, dt)}
 
 
+def cpu_serial_baseline(L=4096, sweeps=8):
+    """The same oracle on one host thread (the paper's CPU reference was
+    serial), in a child process so that OpenMP starts with one thread."""
+    code = ("import sys, time; sys.path.insert(0, %r); import oracle; "
+            "s = oracle.Sim(%d, 1.0, 0.0, %d); s.sweep(1); t = time.perf_counter(); "
+            "s.sweep(%d); print(time.perf_counter() - t)" % (ROOT, L, SEED, sweeps))
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                         timeout=600)
+    dt = float(out.stdout.strip().splitlines()[-1])
+    return {"value": L * L * sweeps / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "L=%d, %d sweeps after one, one thread (%.1f s)" % (L, sweeps, dt)}
+
+
 def run_reference(args, world, rank):
     """--impl reference: the CPU oracle timed on the host cores (rank 0 only)."""
     if rank != 0:
@@ -365,6 +379,7 @@ def run_gpu(args, world, rank, local):
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
+        line["cpu_baseline_serial"] = cpu_serial_baseline()
     print(json.dumps(line), flush=True)
 
 
