@@ -19,10 +19,40 @@ namespace okz {
 
 namespace {
 
+// Philox4x32-10 of counter (c0, c1, c2, c3) with the slot's round keys in
+// shared memory (k[2r], k[2r+1] for round r): one 8-byte broadcast load per
+// round instead of two adds of the key schedule (the key is the slot's seed,
+// the same for the whole CTA).
+__device__ __forceinline__ u32x4 philox10_sm(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                             const uint32_t *__restrict__ rks) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    uint32_t kx, ky;  // loaded round by round (volatile keeps the loads from piling up)
+    asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];"
+                 : "=r"(kx), "=r"(ky)
+                 : "r"((uint32_t)__cvta_generic_to_shared(rks + 2 * r)));
+    const uint2 k = make_uint2(kx, ky);
+    const uint64_t pa = (uint64_t)kPhiloxMulA * c0;
+    const uint64_t pb = (uint64_t)kPhiloxMulB * c2;
+    const uint32_t n0 = (uint32_t)(pb >> 32) ^ c1 ^ k.x;
+    const uint32_t n2 = (uint32_t)(pa >> 32) ^ c3 ^ k.y;
+    c1 = (uint32_t)pb;
+    c3 = (uint32_t)pa;
+    c0 = n0;
+    c2 = n2;
+  }
+  u32x4 out;
+  out.v[0] = c0;
+  out.v[1] = c1;
+  out.v[2] = c2;
+  out.v[3] = c3;
+  return out;
+}
+
 // One 128-site group (4 words) of half-sweep s, in place on B.
 template <bool LAZY>
 __device__ __forceinline__ void group_update(uint32_t *B, int L, int W, uint32_t g, int s,
-                                             uint32_t t, uint64_t seed, const Accept &acc,
+                                             uint32_t t, const uint32_t *rks, const Accept &acc,
                                              int &dH0) {
   uint32_t mn[4], mx[4], ctr[4];
   uint32_t idx[4];
@@ -55,7 +85,7 @@ __device__ __forceinline__ void group_update(uint32_t *B, int L, int W, uint32_t
   for (int m = 0; m < acc.k; ++m) {
     if (((eqp[0] | eqq[0]) | (eqp[1] | eqq[1]) | (eqp[2] | eqq[2]) | (eqp[3] | eqq[3])) == 0u)
       break;
-    const u32x4 rb = group_bits((uint64_t)g, t, (uint32_t)m, seed);
+    const u32x4 rb = philox10_sm(g, 0u, t, (uint32_t)m, rks);
     const uint32_t pb = (uint32_t)(acc.P >> (acc.k - 1 - m)) & 1u;
     const uint32_t qb = (uint32_t)(acc.Q >> (acc.k - 1 - m)) & 1u;
 #pragma unroll
@@ -74,7 +104,7 @@ __device__ __forceinline__ void group_update(uint32_t *B, int L, int W, uint32_t
 
 // Acceptance of 4 words (lazy, bit-sliced U < P / U < Q) -> flips.
 __device__ __forceinline__ void accept4(const uint32_t mn[4], const uint32_t mx[4], uint32_t g,
-                                        uint32_t t, uint64_t seed, const Accept &acc,
+                                        uint32_t t, const uint32_t *rks, const Accept &acc,
                                         uint32_t f[4]) {
   const uint64_t full = 1ull << acc.k;
   uint32_t ltp[4], eqp[4], ltq[4], eqq[4];
@@ -88,7 +118,7 @@ __device__ __forceinline__ void accept4(const uint32_t mn[4], const uint32_t mx[
   for (int m = 0; m < acc.k; ++m) {
     if (((eqp[0] | eqq[0]) | (eqp[1] | eqq[1]) | (eqp[2] | eqq[2]) | (eqp[3] | eqq[3])) == 0u)
       break;
-    const u32x4 rb = group_bits((uint64_t)g, t, (uint32_t)m, seed);
+    const u32x4 rb = philox10_sm(g, 0u, t, (uint32_t)m, rks);
     const uint32_t pb = (uint32_t)(acc.P >> (acc.k - 1 - m)) & 1u;
     const uint32_t qb = (uint32_t)(acc.Q >> (acc.k - 1 - m)) & 1u;
 #pragma unroll
@@ -108,7 +138,8 @@ __device__ __forceinline__ void accept4(const uint32_t mn[4], const uint32_t mx[
 template <bool POW2>
 __device__ __forceinline__ void row_group_update(uint32_t *B, int L, int W, uint32_t gpr,
                                                  int lg_gpr, uint32_t g, int s, uint32_t t,
-                                                 uint64_t seed, const Accept &acc, int &dH0) {
+                                                 const uint32_t *rks, const Accept &acc,
+                                                 int &dH0) {
   const uint32_t y = POW2 ? (g >> lg_gpr) : (g / gpr);
   const uint32_t w0 = 4 * (g - y * gpr);
   const uint32_t yd = (y == 0) ? L - 1 : y - 1, yu = (y == (uint32_t)L - 1) ? 0 : y + 1;
@@ -134,15 +165,15 @@ __device__ __forceinline__ void row_group_update(uint32_t *B, int L, int W, uint
     mx[j] = a & dl & dr & dd & du;
   }
   uint32_t f[4];
-  accept4(mn, mx, g, t, seed, acc, f);
+  accept4(mn, mx, g, t, rks, acc, f);
   if ((f[0] | f[1] | f[2] | f[3]) != 0u)
     *(uint4 *)(row + w0) = make_uint4(c[0] ^ f[0], c[1] ^ f[1], c[2] ^ f[2], c[3] ^ f[3]);
   if (g == 0 && (f[0] & 1u)) dH0 += (mn[0] & 1u) ? 2 : -2;  // site (0,0)
 }
 
 // `n` sweeps of one lattice by the whole CTA.
-__device__ __forceinline__ void cta_sweeps(uint32_t *B, int L, uint32_t t0, int n, uint64_t seed,
-                                           const Accept &acc, int &dH0) {
+__device__ __forceinline__ void cta_sweeps(uint32_t *B, int L, uint32_t t0, int n,
+                                           const uint32_t *rks, const Accept &acc, int &dH0) {
   const int W = L >> 5;
   const uint32_t groups = (uint32_t)L * (uint32_t)W / 4;
   if ((L & 127) == 0) {  // groups never straddle rows
@@ -154,10 +185,10 @@ __device__ __forceinline__ void cta_sweeps(uint32_t *B, int L, uint32_t t0, int 
       for (int s = 0; s < 2; ++s) {
         if (pow2) {
           for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x)
-            row_group_update<true>(B, L, W, gpr, lg, g, s, t, seed, acc, dH0);
+            row_group_update<true>(B, L, W, gpr, lg, g, s, t, rks, acc, dH0);
         } else {
           for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x)
-            row_group_update<false>(B, L, W, gpr, lg, g, s, t, seed, acc, dH0);
+            row_group_update<false>(B, L, W, gpr, lg, g, s, t, rks, acc, dH0);
         }
         __syncthreads();
       }
@@ -168,7 +199,7 @@ __device__ __forceinline__ void cta_sweeps(uint32_t *B, int L, uint32_t t0, int 
     const uint32_t t = t0 + (uint32_t)i;
     for (int s = 0; s < 2; ++s) {
       for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x)
-        group_update<true>(B, L, W, g, s, t, seed, acc, dH0);
+        group_update<true>(B, L, W, g, s, t, rks, acc, dH0);
       __syncthreads();
     }
   }
@@ -182,6 +213,7 @@ batch_sweep_kernel(uint32_t *__restrict__ arena, SlotDesc *__restrict__ slots,
                    uint32_t smem_words) {
   extern __shared__ __align__(16) uint32_t sm[];
   __shared__ int item;
+  __shared__ __align__(8) uint32_t rks[20];  // round keys of the current slot's seed
   const int nwork = work->count;
   while (true) {
     if (threadIdx.x == 0) item = (int)atomicAdd(head, 1u);
@@ -199,13 +231,19 @@ batch_sweep_kernel(uint32_t *__restrict__ arena, SlotDesc *__restrict__ slots,
     acc.Q = d.Q;
     acc.k = d.k;
     int dH0 = 0;
+    if (threadIdx.x < 10) {
+      const uint32_t r = threadIdx.x;
+      rks[2 * r] = (uint32_t)d.seed + r * kPhiloxWeylA;
+      rks[2 * r + 1] = (uint32_t)(d.seed >> 32) + r * kPhiloxWeylB;
+    }
     if (words <= smem_words) {
       for (uint32_t w = threadIdx.x; w < words; w += blockDim.x) sm[w] = g[w];
       __syncthreads();
-      cta_sweeps(sm, d.L, d.t, n, d.seed, acc, dH0);
+      cta_sweeps(sm, d.L, d.t, n, rks, acc, dH0);
       for (uint32_t w = threadIdx.x; w < words; w += blockDim.x) g[w] = sm[w];
     } else {
-      cta_sweeps(g, d.L, d.t, n, d.seed, acc, dH0);
+      __syncthreads();
+      cta_sweeps(g, d.L, d.t, n, rks, acc, dH0);
     }
     if (threadIdx.x == 0) {  // thread 0 owns group 0, the only group with site (0,0)
       slots[slot].t = d.t + (uint32_t)n;
