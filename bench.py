@@ -53,8 +53,8 @@ N_SMS = 152
 #   ddrs_kernel           L = 32768, one launch = 1 sweep
 #   profile_count_kernel  L = 65536, one profile pass
 TRAFFIC = {
-    "parity": ((557193984 + 486310400) / 65536 ** 2, "parity.cu",
-               "11fc9427ebed069d66adf0e1adf9573d4bd6a8e6c864578f603477cd081b1e83"),
+    "parity": ((556859648 + 486997248) / 65536 ** 2, "parity.cu",
+               "c9e16c36adb274aa6415dc4c6289b30fe9b4c28d4178cfb2ae6cf9c2fb898c3b"),
     "ddrs": ((134345472 + 73289472) / 32768 ** 2, "ddrs.cu",
              "6b2f2cbd191834694811fdbf474fc5eb0e73a9edebfc66c6b7baab2356f97324"),
     "profile": ((538082560 + 15609600) / 65536 ** 2, "psd.cu",

@@ -50,7 +50,7 @@ __device__ __forceinline__ void parity_extrema(uint32_t c, uint32_t l, uint32_t 
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256)
 parity_halfsweep_kernel(uint32_t *__restrict__ B, int64_t L, int s, uint32_t t,
-                        uint64_t seed, Accept acc, Ctrl *__restrict__ ctrl) {
+                        const RoundKeys rk, Accept acc, Ctrl *__restrict__ ctrl) {
   const int64_t W = L >> 5;
   const int64_t groups = L * W >> 2;
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -83,7 +83,7 @@ parity_halfsweep_kernel(uint32_t *__restrict__ B, int64_t L, int s, uint32_t t,
   for (int m = 0; m < acc.k; ++m) {
     if (((eqp[0] | eqq[0]) | (eqp[1] | eqq[1]) | (eqp[2] | eqq[2]) | (eqp[3] | eqq[3])) == 0u)
       break;
-    const u32x4 r = group_bits((uint64_t)g, t, (uint32_t)m, seed);
+    const u32x4 r = philox10_rk((uint32_t)g, (uint32_t)((uint64_t)g >> 32), t, (uint32_t)m, rk);
     const uint32_t pb = (uint32_t)(acc.P >> (acc.k - 1 - m)) & 1u;
     const uint32_t qb = (uint32_t)(acc.Q >> (acc.k - 1 - m)) & 1u;
 #pragma unroll
@@ -104,8 +104,8 @@ parity_halfsweep_kernel(uint32_t *__restrict__ B, int64_t L, int s, uint32_t t,
 cudaError_t launch_parity_halfsweep(uint32_t *B, int64_t L, int s, uint32_t t, uint64_t seed,
                                     const Accept &acc, Ctrl *ctrl, cudaStream_t st) {
   const int64_t groups = L * (L >> 5) / 4;
-  parity_halfsweep_kernel<<<(unsigned)((groups + 255) / 256), 256, 0, st>>>(B, L, s, t, seed,
-                                                                              acc, ctrl);
+  parity_halfsweep_kernel<<<(unsigned)((groups + 255) / 256), 256, 0, st>>>(
+      B, L, s, t, round_keys(seed), acc, ctrl);
   return cudaGetLastError();
 }
 
