@@ -54,7 +54,7 @@ N_SMS = 152
 #   profile_count_kernel  L = 65536, one profile pass
 TRAFFIC = {
     "parity": ((556859648 + 486997248) / 65536 ** 2, "parity.cu",
-               "c9e16c36adb274aa6415dc4c6289b30fe9b4c28d4178cfb2ae6cf9c2fb898c3b"),
+               "58bfe093bcdb5ae0e3a445f9fd5bb15d1240f77b8eec6eb406301139af284c2e"),
     "ddrs": ((134345472 + 73289472) / 32768 ** 2, "ddrs.cu",
              "6b2f2cbd191834694811fdbf474fc5eb0e73a9edebfc66c6b7baab2356f97324"),
     "profile": ((538082560 + 15609600) / 65536 ** 2, "psd.cu",

@@ -48,16 +48,17 @@ cudaError_t launch_colscan(const uint32_t *planes, int64_t L, bool parity, int64
 cudaError_t launch_heights(const uint32_t *planes, int64_t L, bool parity, int64_t y0,
                            int64_t ny, int64_t *hcol, int32_t *out, Ctrl *ctrl,
                            cudaStream_t st);
-// Height-parity plane (parity.cu): half-sweeps, fused stream sweeps, and the
-// conversions to and from the slope planes of the C-ABI state format.
+// Height-parity plane: half-sweeps and fused stream sweeps (parity.cu), the
+// blocked random-sequential sweep (ddrs.cu), and the conversions to and from
+// the slope planes of the C-ABI state format (convert.cu).
 cudaError_t launch_parity_halfsweep(uint32_t *B, int64_t L, int s, uint32_t t, uint64_t seed,
                                     const Accept &acc, Ctrl *ctrl, cudaStream_t st);
 cudaError_t launch_parity_stream(const uint32_t *src, uint32_t *dst, int64_t L, uint32_t t,
                                  uint64_t seed, const Accept &acc, int wpt, int fuse,
                                  Ctrl *ctrl, cudaStream_t st);
-cudaError_t launch_to_slopes(const uint32_t *B, int64_t L, uint32_t *out, cudaStream_t st);
 cudaError_t launch_ddrs(uint32_t *B, int64_t L, uint32_t t, uint64_t seed, uint64_t P32,
                         uint64_t Q32, Ctrl *ctrl, cudaStream_t st);
+cudaError_t launch_to_slopes(const uint32_t *B, int64_t L, uint32_t *out, cudaStream_t st);
 cudaError_t launch_from_slopes(const uint32_t *slopes, int64_t L, long long H0, int64_t *bcol,
                                uint32_t *B, cudaStream_t st);
 

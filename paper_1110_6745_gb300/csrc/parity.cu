@@ -15,7 +15,7 @@
 //
 // Layout: L rows of L/32 little-endian uint32 words; bit b of word w of row y
 // is site x = 32w + b. The C-ABI state format stays the slope planes;
-// to_slopes / from_slopes convert at the boundary.
+// convert.cu converts at the boundary.
 #include <cuda_runtime.h>
 
 #include "okz_internal.h"
