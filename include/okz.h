@@ -118,7 +118,11 @@ typedef struct okz_sim okz_sim;
 /* Fills *prm with the defaults: L = 0, p = 1, q = 0, seed = 0, s_sel = 0.5,
  * k_max = 32, kernel = AUTO, words_per_thread = 0, sweeps_per_pass = 0. The
  * last two only choose how the stream kernel tiles the work; results are
- * bit-identical for every choice. */
+ * bit-identical for every choice. Their automatic values (measured best on
+ * GB300): parity plane -- 8 words per thread from L = 16384 up where
+ * L % 8192 == 0, else 4; two sweeps per pass with k = 1, one with k >= 2;
+ * slope planes -- 8 words per thread where L % 8192 == 0, else 4; one sweep
+ * per pass. */
 void okz_params_init(okz_params *prm);
 
 /* Device bytes a simulation of size L needs when memory is passed to
