@@ -1,4 +1,9 @@
-"""Steady-state statistics across replicas (Kelling & Odor, Secs. III and IV).
+"""Growth series and steady-state statistics (Kelling & Odor, Secs. III and IV).
+
+* The growth run: W^2 at log-spaced sample times (the paper's Eq. (8)
+  recursion read as n log-spaced times over T), the growth exponent beta as
+  the slope of (1/2) ln(W^2 - W^2(0)) against ln t (Sec. III), and its local
+  slopes beta_eff (Eq. (11)).
 
 * The distribution of the squared width W^2 in the steady state: its
   cumulants kappa_1..kappa_4, written through the raw moments
@@ -14,6 +19,8 @@ Samples come from batched replicas (okz_batch_*): every replica is run to the
 steady state and then sampled every `every` sweeps; each W^2 sample is exact
 (Eq. (4)), each spectrum is computed on the device (okz_psd).
 """
+import math
+
 import numpy as np
 
 import paper_1110_6745_gb300 as okz
@@ -115,3 +122,65 @@ def spectrum_slope(S, kmin, kmax):
     k = np.arange(len(S))
     m = (k >= kmin) & (k <= kmax)
     return float(np.polyfit(np.log(k[m]), np.log(np.asarray(S)[m]), 1)[0])
+
+
+def sample_times(T, n):
+    """[0] + n log-spaced sweep counts over T: t_j = max(round(T^(j/(n-1))),
+    t_(j-1) + 1), j = 0 .. n-1, rounding halves away from zero (so t_(n-1) = T).
+    Requires 2 <= n <= T."""
+    T, n = int(T), int(n)
+    if n < 2 or n > T:
+        raise ValueError("need 2 <= n <= T")
+    out, prev = [0], 0
+    for j in range(n):
+        v = int(math.floor(math.pow(float(T), j / (n - 1)) + 0.5))
+        v = max(v, prev + 1)
+        out.append(v)
+        prev = v
+    if out[-1] != T:
+        raise ValueError("the schedule does not end at T")
+    return out
+
+
+def growth_series(L, T, n, p=1.0, q=0.0, seed=0, s_sel=0.5, kernel=None):
+    """A growth run from the striped start: one simulation swept to every
+    sample time of sample_times(T, n); returns records (t, H0, S1, S2, W2)
+    with the exact sums of h and h^2 (Eq. (4))."""
+    kw = {} if kernel is None else {"kernel": kernel}
+    rec = []
+    with okz.Simulation(L, p, q, seed=seed, s_sel=s_sel, **kw) as sim:
+        done = 0
+        for t in sample_times(T, n):
+            sim.sweep(t - done)
+            done = t
+            S1, S2, W2 = sim.width2()
+            rec.append((t, sim.info().H0, S1, S2, W2))
+    return rec
+
+
+def beta_fit(t, w2, tmin, tmax, w2_0=0.25):
+    """Least-squares slope of (1/2) ln(W^2 - w2_0) against ln t over
+    tmin <= t <= tmax (Sec. III: the constant W^2(0) = 1/4 of the striped start
+    is subtracted first)."""
+    t = np.asarray(t, dtype=np.float64)
+    w2 = np.asarray(w2, dtype=np.float64)
+    m = (t >= tmin) & (t <= tmax)
+    return float(np.polyfit(np.log(t[m]), 0.5 * np.log(w2[m] - w2_0), 1)[0])
+
+
+def beta_eff(t, w2, ratio=2.0, w2_0=0.25):
+    """Local slopes of Eq. (11): beta_eff(t) = [ln W(t) - ln W(t')] /
+    [ln t - ln t'] with W^2 - w2_0 for W^2 and t' the latest sample time
+    <= t / ratio. Returns (t values, beta_eff) for every t that has such a t'
+    > 0."""
+    ts = [float(x) for x in t]
+    w = [float(x) - w2_0 for x in w2]
+    out_t, out_b = [], []
+    for i, ti in enumerate(ts):
+        prev = [j for j in range(i) if 0 < ts[j] <= ti / ratio]
+        if not prev:
+            continue
+        j = prev[-1]
+        out_t.append(ti)
+        out_b.append(0.5 * (math.log(w[i]) - math.log(w[j])) / (math.log(ti) - math.log(ts[j])))
+    return np.array(out_t), np.array(out_b)

@@ -76,6 +76,25 @@ def test_spectrum_slope_of_a_power_law():
     assert spectrum_slope(S, 2, 100) == pytest.approx(-2.786, abs=1e-12)
 
 
+def test_sample_times_match_the_oracle(orc):
+    """The product's schedule and the oracle's (written independently from
+    the same reading of the paper's sampling times) agree."""
+    from paper_1110_6745_gb300.analysis import sample_times
+    for T, n in [(1000, 20), (10000, 40), (8192, 32), (7, 7), (2, 2), (123457, 60)]:
+        assert sample_times(T, n) == orc.sample_times(T, n), (T, n)
+    with pytest.raises(ValueError):
+        sample_times(5, 6)
+
+
+def test_beta_fit_and_local_slopes_of_a_power_law():
+    from paper_1110_6745_gb300.analysis import beta_eff, beta_fit, sample_times
+    t = np.array(sample_times(10000, 40)[1:], float)
+    w2 = 0.25 + 0.7 * t ** (2 * 0.2415)
+    assert beta_fit(t, w2, 200, 10000) == pytest.approx(0.2415, abs=1e-12)
+    tt, b = beta_eff(t, w2)
+    assert len(tt) > 20 and np.allclose(b, 0.2415, atol=1e-12)
+
+
 @pytest.mark.gpu
 def test_steady_state_sampler_matches_single_runs():
     import torch

@@ -175,6 +175,17 @@ def test_growth_series_L256(okz, orc, kernel):
         _compare(sim, ref)
 
 
+def test_growth_series_helper_matches_oracle(okz, orc):
+    """analysis.growth_series (the product's sampling loop) at L = 256,
+    1000 sweeps, 20 samples: every record equals the oracle's."""
+    from paper_1110_6745_gb300.analysis import growth_series
+    rec = growth_series(256, 1000, 20, p=1.0, q=0.0, seed=1)
+    ref = orc.Sim(256, 1.0, 0.0, 1)
+    for t, H0, S1, S2, W2 in rec:
+        ref.sweep(t - ref.t)
+        assert (H0, S1, S2, W2) == (ref.H0, *ref.sums(), ref.width2()), t
+
+
 def test_checkpoint_resume_is_exact(okz):
     for L, kernel in [(256, 1), (8192, 2), (256, 3), (8192, 4)]:
         a = okz.Simulation(L, 0.75, 0.25, seed=9, kernel=kernel)
