@@ -37,10 +37,12 @@ BYTES_PER_SITE_LAUNCH = {"slope": 0.5, "parity": 0.25}
 KERNELS = {"auto": 0, "slope": 2, "parity": 4}
 
 # Integer work of one sweep of the parity-plane kernel, per site (the ALU roof):
-# per 32-site word and half-sweep 2 funnel shifts + 4 three-input logic ops +
-# 1 xor = 7 ALU-pipe ops; per 128-site Philox4x32-10 block 20 three-input xors
-# (ALU pipe) and 20 32x32->64 multiplies (FMA pipe).
-ALU_OPS_PER_SITE_SWEEP = {"parity": 2 * 7 / 32 + 20 / 128,
+# per 32-site word and half-sweep 2 funnel shifts (left and right neighbours)
+# + 4 three-input logic ops (the two neighbour tests, then y & a & ~r0 and
+# c ^ (x & that): the new word depends on 7 inputs with c used five times, so
+# no 3-op form exists) = 6 ALU-pipe ops; per 128-site Philox4x32-10 block 20
+# three-input xors (ALU pipe) and 20 32x32->64 multiplies (FMA pipe).
+ALU_OPS_PER_SITE_SWEEP = {"parity": 2 * 6 / 32 + 20 / 128,
                           "slope": 2 * 9 / 32 + 20 / 128}
 ALU_LANES_PER_SM = 64  # INT32 ALU-pipe lanes per SM per clock (16 per sub-partition)
 N_SMS = 152

@@ -130,7 +130,7 @@ struct PModes {
   uint32_t p1, p2, q1, q2;  // k <= 1: all-ones masks for "bit must be 0" and "always"
 };
 
-// Flips of WPT words of one stage of half-sweep parity SP. The neighbour
+// New words (o) of WPT words of one stage of half-sweep parity SP. The neighbour
 // tests use 3-input logic: for SP = 0 a minimum has all four neighbours equal
 // to its own bit ("both equal" table 0x81 on (l, r, c) and on (d, u, c)),
 // for SP = 1 all four differ (table 0x42); maxima are the reverse.
@@ -139,7 +139,7 @@ __device__ __forceinline__ void pstage(const uint32_t c[WPT], uint32_t lbit, uin
                                        const uint32_t d[WPT], const uint32_t u[WPT], uint32_t a,
                                        const uint32_t (&lv)[KC][WPT], uint32_t g0, uint32_t t,
                                        const RoundKeys &rk, const Accept &acc,
-                                       const PModes &md, uint32_t f[WPT], uint32_t *mn0) {
+                                       const PModes &md, uint32_t o[WPT], uint32_t *mn0) {
   const uint32_t *r0 = lv[0];
   constexpr uint32_t kMin = SP ? 0x42u : 0x81u;
   constexpr uint32_t kMax = SP ? 0x81u : 0x42u;
@@ -149,8 +149,10 @@ __device__ __forceinline__ void pstage(const uint32_t c[WPT], uint32_t lbit, uin
     const uint32_t l = __funnelshift_l(j == 0 ? (lbit << 31) : c[j - 1], c[j], 1);
     const uint32_t r = __funnelshift_r(c[j], j == WPT - 1 ? rbit : c[j + 1], 1);
     if (MODE == kPModeHalf) {
-      const uint32_t ar = a & ~r0[j];  // active and selected by the level-0 bit
-      f[j] = lop3<0x80>(lop3<kMin>(l, r, c[j]), lop3<kMin>(d[j], u[j], c[j]), ar);
+      // new word = c ^ (x & y & a & ~r0): y & a & ~r0 (table 0x40), then
+      // c ^ (x & that) (table 0x78) -- 2 funnel shifts + 4 logic ops per word
+      const uint32_t ysel = lop3<0x40>(lop3<kMin>(d[j], u[j], c[j]), a, r0[j]);
+      o[j] = lop3<0x78>(c[j], lop3<kMin>(l, r, c[j]), ysel);
     } else {
       mn[j] = lop3<0x80>(lop3<kMin>(l, r, c[j]), lop3<kMin>(d[j], u[j], c[j]), a);
       mx[j] = lop3<0x80>(lop3<kMax>(l, r, c[j]), lop3<kMax>(d[j], u[j], c[j]), a);
@@ -164,7 +166,7 @@ __device__ __forceinline__ void pstage(const uint32_t c[WPT], uint32_t lbit, uin
   if (MODE == kPModeK1) {
 #pragma unroll
     for (int j = 0; j < WPT; ++j)
-      f[j] = (mn[j] & ((~r0[j] & md.p1) | md.p2)) | (mx[j] & ((~r0[j] & md.q1) | md.q2));
+      o[j] = c[j] ^ ((mn[j] & ((~r0[j] & md.p1) | md.p2)) | (mx[j] & ((~r0[j] & md.q1) | md.q2)));
   } else {
     const uint64_t full = 1ull << acc.k;
     uint32_t ltp[WPT], eqp[WPT], ltq[WPT], eqq[WPT];
@@ -219,7 +221,7 @@ __device__ __forceinline__ void pstage(const uint32_t c[WPT], uint32_t lbit, uin
       }
     }
 #pragma unroll
-    for (int j = 0; j < WPT; ++j) f[j] = ltp[j] | ltq[j];
+    for (int j = 0; j < WPT; ++j) o[j] = c[j] ^ (ltp[j] | ltq[j]);
   }
 }
 
@@ -354,17 +356,17 @@ parity_stream_kernel(const uint32_t *__restrict__ src, uint32_t *__restrict__ ds
         const uint32_t *u = (h == 0) ? cu : out[h > 0 ? h - 1 : 0];
         const uint32_t lbit = (h == 0) ? lb : WL[h > 0 ? h - 1 : 0];
         const uint32_t rbit = (h == 0) ? rb : WR[h > 0 ? h - 1 : 0];
-        uint32_t f[WPT];
+        uint32_t o[WPT];
         // s = 1 uses the words of the same row drawn by stage h-1 last step
         if (s == 0)
           pstage<WPT, MODE, 0, KC>(c, lbit, rbit, d, u, am, Rn[h >> 1], g0, t, rk, acc, md,
-                                   f, &mn0[h]);
+                                   o, &mn0[h]);
         else
           pstage<WPT, MODE, 1, KC>(c, lbit, rbit, d, u, am, R[h >> 1], g0, t, rk, acc, md,
-                                   f, &mn0[h]);
-        fbit[h] = f[0] & 1u;
+                                   o, &mn0[h]);
+        fbit[h] = (o[0] ^ c[0]) & 1u;
 #pragma unroll
-        for (int j = 0; j < WPT; ++j) out[h][j] = c[j] ^ f[j];
+        for (int j = 0; j < WPT; ++j) out[h][j] = o[j];
         if (s == 1) {
 #pragma unroll
           for (int m = 0; m < KC; ++m)
