@@ -55,8 +55,8 @@ N_SMS = 152
 #   ddrs_kernel           L = 32768, one launch = 1 sweep
 #   profile_count_kernel  L = 65536, one profile pass
 TRAFFIC = {
-    "parity": ((556859648 + 486997248) / 65536 ** 2, "parity.cu",
-               "58bfe093bcdb5ae0e3a445f9fd5bb15d1240f77b8eec6eb406301139af284c2e"),
+    "parity": ((556863744 + 489195264) / 65536 ** 2, "parity.cu",
+               "403218eb2d93ef4257a188a55fb71ccde776997d9b730214a931650619d0ba4e"),
     "ddrs": ((134345472 + 73289472) / 32768 ** 2, "ddrs.cu",
              "6b2f2cbd191834694811fdbf474fc5eb0e73a9edebfc66c6b7baab2356f97324"),
     "profile": ((538082560 + 15609600) / 65536 ** 2, "psd.cu",
