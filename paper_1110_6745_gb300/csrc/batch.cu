@@ -135,11 +135,12 @@ __device__ __forceinline__ void accept4(const uint32_t mn[4], const uint32_t mx[
 // row below, row above), 2 neighbour words, 1 vector store. Whole-word
 // stores are safe: every bit another thread reads from these words sits on a
 // site this half-sweep does not move.
-template <bool POW2>
+template <bool POW2, int SP>
 __device__ __forceinline__ void row_group_update(uint32_t *B, int L, int W, uint32_t gpr,
-                                                 int lg_gpr, uint32_t g, int s, uint32_t t,
+                                                 int lg_gpr, uint32_t g, uint32_t t,
                                                  const uint32_t *rks, const Accept &acc,
                                                  int &dH0) {
+  constexpr int s = SP;
   const uint32_t y = POW2 ? (g >> lg_gpr) : (g / gpr);
   const uint32_t w0 = 4 * (g - y * gpr);
   const uint32_t yd = (y == 0) ? L - 1 : y - 1, yu = (y == (uint32_t)L - 1) ? 0 : y + 1;
@@ -152,17 +153,19 @@ __device__ __forceinline__ void row_group_update(uint32_t *B, int L, int W, uint
   const uint32_t c[4] = {cv.x, cv.y, cv.z, cv.w};
   const uint32_t d[4] = {dv.x, dv.y, dv.z, dv.w};
   const uint32_t u[4] = {uv.x, uv.y, uv.z, uv.w};
-  const uint32_t S = s ? ~0u : 0u;
   const uint32_t a = active_mask(y, s);
+  // a minimum of half-sweep s has all four neighbours equal to its own bit
+  // xor s: "both equal" (table 0x81) for s = 0, "both differ" (0x42) for
+  // s = 1, on (l, r, c) and (d, u, c); a maximum the reverse
+  constexpr uint32_t kMin = SP ? 0x42u : 0x81u;
+  constexpr uint32_t kMax = SP ? 0x81u : 0x42u;
   uint32_t mn[4], mx[4];
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     const uint32_t l = __funnelshift_l(j == 0 ? lw : c[j - 1], c[j], 1);
     const uint32_t r = __funnelshift_r(c[j], j == 3 ? rw : c[j + 1], 1);
-    const uint32_t cc = c[j] ^ S;
-    const uint32_t dl = l ^ cc, dr = r ^ cc, dd = d[j] ^ cc, du = u[j] ^ cc;
-    mn[j] = a & ~(dl | dr | dd | du);
-    mx[j] = a & dl & dr & dd & du;
+    mn[j] = lop3<0x80>(lop3<kMin>(l, r, c[j]), lop3<kMin>(d[j], u[j], c[j]), a);
+    mx[j] = lop3<0x80>(lop3<kMax>(l, r, c[j]), lop3<kMax>(d[j], u[j], c[j]), a);
   }
   uint32_t f[4];
   accept4(mn, mx, g, t, rks, acc, f);
@@ -182,16 +185,20 @@ __device__ __forceinline__ void cta_sweeps(uint32_t *B, int L, uint32_t t0, int 
     const int lg = __ffs(gpr) - 1;
     for (int i = 0; i < n; ++i) {
       const uint32_t t = t0 + (uint32_t)i;
-      for (int s = 0; s < 2; ++s) {
-        if (pow2) {
-          for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x)
-            row_group_update<true>(B, L, W, gpr, lg, g, s, t, rks, acc, dH0);
-        } else {
-          for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x)
-            row_group_update<false>(B, L, W, gpr, lg, g, s, t, rks, acc, dH0);
-        }
+      if (pow2) {
+        for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x)
+          row_group_update<true, 0>(B, L, W, gpr, lg, g, t, rks, acc, dH0);
         __syncthreads();
+        for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x)
+          row_group_update<true, 1>(B, L, W, gpr, lg, g, t, rks, acc, dH0);
+      } else {
+        for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x)
+          row_group_update<false, 0>(B, L, W, gpr, lg, g, t, rks, acc, dH0);
+        __syncthreads();
+        for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x)
+          row_group_update<false, 1>(B, L, W, gpr, lg, g, t, rks, acc, dH0);
       }
+      __syncthreads();
     }
     return;
   }
