@@ -55,8 +55,8 @@ N_SMS = 152
 #   ddrs_kernel           L = 32768, one launch = 1 sweep
 #   profile_count_kernel  L = 65536, one profile pass
 TRAFFIC = {
-    "parity": ((556863744 + 489195264) / 65536 ** 2, "parity.cu",
-               "403218eb2d93ef4257a188a55fb71ccde776997d9b730214a931650619d0ba4e"),
+    "parity": ((556869376 + 485988608) / 65536 ** 2, "parity.cu",
+               "804ee68040f74f9233afa4baa5220f61551c75144c1729f71dd97aabe8a6d5ba"),
     "ddrs": ((134345472 + 73289472) / 32768 ** 2, "ddrs.cu",
              "6b2f2cbd191834694811fdbf474fc5eb0e73a9edebfc66c6b7baab2356f97324"),
     "profile": ((538082560 + 15609600) / 65536 ** 2, "psd.cu",
@@ -74,6 +74,21 @@ def _traffic(name, sites):
     if hashlib.sha256(open(path, "rb").read()).hexdigest() != sha:
         return None
     return per_site * sites
+
+
+def _size_label(L):
+    """'2^17 (2^34 sites)' for a power of two, else '98304 (9663676416 sites)'."""
+    if L & (L - 1) == 0:
+        e = L.bit_length() - 1
+        return "2^%d (2^%d sites)" % (e, 2 * e)
+    return "%d (%d sites)" % (L, L * L)
+
+
+def _bytes_label(n):
+    for unit, size in (("GiB", 1 << 30), ("MiB", 1 << 20), ("KiB", 1 << 10)):
+        if n >= size:
+            return "%g %s" % (n / size, unit)
+    return "%d B" % n
 
 
 def _peaks():
@@ -353,10 +368,12 @@ def run_gpu(args, world, rank, local):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic",
-        "config": {"workload": "octahedron growth run L=2^17 (2^34 sites), striped start, "
-                               "p=1 q=0 s_sel=1/2, seed=11; step = 256 sweeps + exact W^2",
+        "config": {"workload": "octahedron growth run L=%s, striped start, "
+                               "p=1 q=0 s_sel=1/2, seed=11; step = %d sweeps + exact W^2"
+                               % (_size_label(L), SWEEPS_PER_STEP),
                    "L": L, "sweeps_per_step": SWEEPS_PER_STEP, "t_range": [0, sweeps],
-                   "l2": "inputs larger than L2 (2 x 4 GiB ping-pong planes)",
+                   "l2": "inputs larger than L2 (2 x %s ping-pong planes)"
+                         % _bytes_label(L * L // (8 if repr_name == "parity" else 4)),
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak,
                      "unit": "Tops/s", "frac": alu_achieved / alu_peak,

@@ -97,7 +97,8 @@ typedef struct okz_params {
     double s_sel;   /* selection probability of an active site, (0, 1]; 0.5      */
     int32_t k_max;  /* largest acceptance precision in bits, 1..32; 32            */
     int32_t kernel; /* OKZ_KERNEL_*                                                */
-    int32_t words_per_thread; /* STREAM: 4 or 8 words of 32 sites per thread; 0 = auto */
+    int32_t words_per_thread; /* STREAM: 4, 8 (or 16, parity plane) words of 32 sites
+                                 per thread; 0 = auto                                */
     int32_t sweeps_per_pass;  /* STREAM: 1 or 2 sweeps fused per launch; 0 = auto      */
 } okz_params;
 
@@ -118,9 +119,11 @@ typedef struct okz_sim okz_sim;
 /* Fills *prm with the defaults: L = 0, p = 1, q = 0, seed = 0, s_sel = 0.5,
  * k_max = 32, kernel = AUTO, words_per_thread = 0, sweeps_per_pass = 0. The
  * last two only choose how the stream kernel tiles the work; results are
- * bit-identical for every choice. Their automatic values (measured best on
- * GB300): parity plane -- 8 words per thread from L = 16384 up where
- * L % 8192 == 0, else 4; two sweeps per pass with k = 1, one with k >= 2;
+ * bit-identical for every choice. 8 words per thread needs L % 8192 == 0,
+ * 16 (parity stream kernel only) L % 16384 == 0. Their automatic values
+ * (measured best on GB300): parity plane -- with k = 1, 16 words per thread
+ * from L = 32768 up, with k >= 2, 8 from L = 65536 up, else 4 (or the next
+ * smaller valid choice); two sweeps per pass with k = 1, one with k >= 2;
  * slope planes -- 8 words per thread where L % 8192 == 0, else 4; one sweep
  * per pass. */
 void okz_params_init(okz_params *prm);

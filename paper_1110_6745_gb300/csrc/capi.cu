@@ -171,21 +171,35 @@ okz_status okz_create_ex(const okz_params *prm, void *dev_buf, size_t bytes, voi
   int wpt = prm->words_per_thread, fuse = prm->sweeps_per_pass;
   if (streamed) {
     // defaults measured on GB300. Slope planes: 8 words per thread where the
-    // row allows it, one sweep per pass. Parity plane: 8 words per thread
-    // from L = 16384 up (4 below: a CTA spans one short row, and 4 words per
-    // thread doubles its threads); two sweeps per pass with one random level
-    // per site (k = 1), one sweep per pass with k >= 2 (the fused general-k
-    // kernels hold too many registers: one pass per sweep is 8-30 % faster)
+    // row allows it, one sweep per pass. Parity plane with one random level
+    // per site (k = 1): 16 words per thread from L = 32768 up (256 threads
+    // a row at L = 2^17, each with twice the independent words of the
+    // 8-word kernel: 8-12 % faster), 4 below (a CTA spans one short row, and
+    // 4 words per thread gives it the most threads); with k >= 2, 8 words per
+    // thread from L = 65536 up, else 4 (the 16-word general-k kernels are
+    // 5-15 % slower). Two sweeps per pass with k = 1, one with k >= 2 (the
+    // fused general-k kernels hold too many registers: one pass per sweep is
+    // 8-30 % faster)
     if (kernel == OKZ_KERNEL_PARITY_STREAM) {
-      if (wpt == 0) wpt = (prm->L >= 16384 && stream_wpt_valid(prm->L, 8)) ? 8 : 4;
+      if (wpt == 0) {
+        const int64_t L = prm->L;
+        if (k <= 1 && L >= 32768 && parity_wpt_valid(L, 16))
+          wpt = 16;
+        else if (L >= (k <= 1 ? 32768 : 65536) && stream_wpt_valid(L, 8))
+          wpt = 8;
+        else
+          wpt = 4;
+      }
       if (fuse == 0) fuse = (k >= 2) ? 1 : 2;
     } else {
       if (wpt == 0) wpt = stream_wpt_valid(prm->L, 8) ? 8 : 4;
       if (fuse == 0) fuse = 1;
     }
-    if (!stream_wpt_valid(prm->L, wpt) || (fuse != 1 && fuse != 2)) {
-      set_error("words_per_thread must be 4 or 8 (8 needs L % 8192 == 0) and "
-                "sweeps_per_pass 1 or 2");
+    const bool wpt_ok = kernel == OKZ_KERNEL_PARITY_STREAM ? parity_wpt_valid(prm->L, wpt)
+                                                          : stream_wpt_valid(prm->L, wpt);
+    if (!wpt_ok || (fuse != 1 && fuse != 2)) {
+      set_error("words_per_thread must be 4 or 8 (8 needs L % 8192 == 0; the parity "
+                "stream kernel also takes 16 with L % 16384 == 0) and sweeps_per_pass 1 or 2");
       return OKZ_EINVAL;
     }
   } else {

@@ -53,6 +53,8 @@ cudaError_t launch_heights(const uint32_t *planes, int64_t L, bool parity, int64
 // the slope planes of the C-ABI state format (convert.cu).
 cudaError_t launch_parity_halfsweep(uint32_t *B, int64_t L, int s, uint32_t t, uint64_t seed,
                                     const Accept &acc, Ctrl *ctrl, cudaStream_t st);
+// The parity stream kernel also takes 16 words per thread: L % 16384 == 0.
+bool parity_wpt_valid(int64_t L, int wpt);
 cudaError_t launch_parity_stream(const uint32_t *src, uint32_t *dst, int64_t L, uint32_t t,
                                  uint64_t seed, const Accept &acc, int wpt, int fuse,
                                  Ctrl *ctrl, cudaStream_t st);

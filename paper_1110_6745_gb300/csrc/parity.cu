@@ -227,9 +227,10 @@ __device__ __forceinline__ void pstage(const uint32_t c[WPT], uint32_t lbit, uin
 
 }  // namespace
 
-// SMALL: rows of at most 256 threads (L <= 32768 at 4 words per thread), so
-// the register budget is not capped by a 1024-thread bound; in the general-k
-// mode these kernels also carry random levels 1 and 2 between half-sweeps.
+// SMALL: rows of at most 256 threads (L <= 32768 at 4 words per thread, any
+// L at 16), so the register budget is not capped by a 512- or 1024-thread
+// bound; in the general-k mode the 4-word kernels also carry random levels 1
+// and 2 between half-sweeps.
 template <int WPT, int F, int MODE, bool SMALL>
 __global__ void __launch_bounds__(SMALL ? 256 : (WPT == 4 ? 1024 : 512), 1)
 parity_stream_kernel(const uint32_t *__restrict__ src, uint32_t *__restrict__ dst, int L,
@@ -238,7 +239,7 @@ parity_stream_kernel(const uint32_t *__restrict__ src, uint32_t *__restrict__ ds
   constexpr int NST = 2 * F;
   constexpr int NC = NST > 1 ? NST - 1 : 1;  // stages whose output is carried
   constexpr int NG = WPT / 4;
-  constexpr int KC = (SMALL && MODE == kPModeGen) ? 3 : 1;  // levels drawn once per sweep
+  constexpr int KC = (SMALL && MODE == kPModeGen && WPT == 4) ? 3 : 1;  // levels drawn once per sweep
   extern __shared__ __align__(128) unsigned char smem[];
   const int nthr = blockDim.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -506,6 +507,10 @@ template <int MODE>
 cudaError_t plaunch_mode(const uint32_t *src, uint32_t *dst, int L, uint32_t t, uint64_t seed,
                          const Accept &acc, const PModes &md, int wpt, int fuse, Ctrl *ctrl,
                          cudaStream_t st) {
+  if (wpt == 16) {  // rows of at most 256 threads (parity_wpt_valid)
+    if (fuse == 2) return plaunch<16, 2, MODE, true>(src, dst, L, t, seed, acc, md, ctrl, st);
+    return plaunch<16, 1, MODE, true>(src, dst, L, t, seed, acc, md, ctrl, st);
+  }
   if (wpt == 8) {
     if (fuse == 2) return plaunch<8, 2, MODE>(src, dst, L, t, seed, acc, md, ctrl, st);
     return plaunch<8, 1, MODE>(src, dst, L, t, seed, acc, md, ctrl, st);
@@ -519,6 +524,12 @@ cudaError_t plaunch_mode(const uint32_t *src, uint32_t *dst, int L, uint32_t t, 
 }
 
 }  // namespace
+
+bool parity_wpt_valid(int64_t L, int wpt) {
+  if (wpt == 16)  // L/512 threads: whole warps, at most 256 (the SMALL bound)
+    return stream_kernel_supports(L) && L % 16384 == 0 && L / 512 <= 256;
+  return stream_wpt_valid(L, wpt);
+}
 
 cudaError_t launch_parity_stream(const uint32_t *src, uint32_t *dst, int64_t L, uint32_t t,
                                  uint64_t seed, const Accept &acc, int wpt, int fuse,

@@ -114,6 +114,52 @@ def test_stream_variants_long_run_L32768(okz, wpt, fuse, kernel):
     b.close()
 
 
+@pytest.mark.parametrize("fuse", [1, 2])
+@pytest.mark.parametrize("p,q,s_sel", [(1.0, 0.0, 0.5), (0.75, 0.25, 0.5), (1.0, 1.0, 0.5),
+                                       (0.95, 0.05, 0.5)])
+def test_parity_stream_wpt16_matches_oracle(okz, orc, p, q, s_sel, fuse):
+    """16 words per thread (the smallest row it allows, L = 2^14: one warp per
+    row) gives the oracle's lattice in every acceptance mode."""
+    L, seed = 16384, 41
+    ref = orc.Sim(L, p, q, seed, s_sel=s_sel)
+    with okz.Simulation(L, p, q, seed=seed, s_sel=s_sel, kernel=okz.OKZ_KERNEL_PARITY_STREAM,
+                        words_per_thread=16, sweeps_per_pass=fuse) as sim:
+        assert sim.wpt == 16
+        for n in (1, 2):
+            ref.sweep(n)
+            sim.sweep(n)
+            _compare(sim, ref)
+        S1, S2, W2 = sim.width2()
+        assert (S1, S2) == ref.sums() and W2 == ref.width2()
+
+
+@pytest.mark.parametrize("L,p,q,fuse", [(32768, 1.0, 0.0, 2), (65536, 0.95, 0.05, 1),
+                                        (131072, 1.0, 0.0, 2), (131072, 1.0, 1.0, 2)])
+def test_parity_stream_wpt16_long_run(okz, L, p, q, fuse):
+    """16 words per thread against the 8-word kernel over many sweeps, up to
+    the largest lattice (256 threads per row)."""
+    a = okz.Simulation(L, p, q, seed=12, kernel=okz.OKZ_KERNEL_PARITY_STREAM,
+                       words_per_thread=16, sweeps_per_pass=fuse)
+    b = okz.Simulation(L, p, q, seed=12, kernel=okz.OKZ_KERNEL_PARITY_STREAM,
+                       words_per_thread=8, sweeps_per_pass=fuse)
+    a.sweep(21)
+    b.sweep(21)
+    assert a.width2() == b.width2()
+    pa, ha, ta = a.state()
+    pb, hb, tb = b.state()
+    assert np.array_equal(pa, pb) and (ha, ta) == (hb, tb)
+    a.close()
+    b.close()
+
+
+def test_wpt16_rejected_where_invalid(okz):
+    """16 words per thread needs L % 16384 == 0 and the parity stream kernel."""
+    for L, kernel in ((8192, okz.OKZ_KERNEL_PARITY_STREAM), (12288, okz.OKZ_KERNEL_PARITY_STREAM),
+                      (16384, okz.OKZ_KERNEL_STREAM)):
+        with pytest.raises(okz.OkzError):
+            okz.Simulation(L, 1.0, 0.0, seed=1, kernel=kernel, words_per_thread=16)
+
+
 @pytest.mark.parametrize("kernel", [2, 3, 4])
 @pytest.mark.parametrize("L", [4096, 8192, 16384])
 def test_stream_equals_plain_long_run(okz, L, kernel):
