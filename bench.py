@@ -53,14 +53,14 @@ N_SMS = 152
 # null once the source changes.
 #   parity_stream_kernel  L = 65536, one launch = 2 sweeps
 #   ddrs_kernel           L = 32768, one launch = 1 sweep
-#   profile_count_kernel  L = 65536, one profile pass
+#   profile_count_tma_kernel  L = 65536, one profile pass
 TRAFFIC = {
     "parity": ((556869376 + 485988608) / 65536 ** 2, "parity.cu",
                "804ee68040f74f9233afa4baa5220f61551c75144c1729f71dd97aabe8a6d5ba"),
     "ddrs": ((134345472 + 73289472) / 32768 ** 2, "ddrs.cu",
              "6b2f2cbd191834694811fdbf474fc5eb0e73a9edebfc66c6b7baab2356f97324"),
-    "profile": ((538082560 + 15609600) / 65536 ** 2, "psd.cu",
-                "e006ee1ddc9f3670b621c81c5870b40ffd0229b3359201d9da06bd46e8d03c8a"),
+    "profile": ((537716992 + 3588864) / 65536 ** 2, "psd.cu",
+                "9afb4581b2be7074517c9659a25cb9f6d4c44d90c33260acfc06c55ace912ca6"),
 }
 
 
@@ -564,6 +564,15 @@ def run_rs(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def _fft_launches(L):
+    """Kernels of okz_psd's two transforms: the shared-memory block of the
+    first min(log2 L, 11) stages, a radix-2 stage if an odd number is left,
+    radix-4 steps for the rest (the last also writes S), else a finish."""
+    lg = int(L).bit_length() - 1
+    rem = lg - min(lg, 11)
+    return 1 + rem % 2 + rem // 2 + (1 if rem < 2 else 0)
+
+
 def run_spectrum(args, world, rank, local):
     """--workload spectrum: interface profiles and the axis power spectrum
     (okz_psd) of the L = 2^17 lattice after 64 sweeps; a step = one spectrum."""
@@ -609,17 +618,18 @@ def run_spectrum(args, world, rank, local):
         "ms_per_step": wall / steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32/f64", "data": "synthetic", "impl": "okz-spectrum",
         "config": {"workload": "okz_psd of the L=2^17 lattice after 64 growth sweeps "
-                               "(p=1 q=0 s_sel=1/2, seed=11); host-synchronous call, 3 x 1 MiB "
-                               "device-to-host copies included", "L": L,
+                               "(p=1 q=0 s_sel=1/2, seed=11); host-synchronous call, the 1 MiB "
+                               "device-to-host copy of S included", "L": L,
                    "l2": "inputs larger than L2 (2 GiB parity plane)"},
         "roofline": {"bound": "hbm", "achieved": alg / gpu_s / 1e9, "peak": peak,
                      "unit": "GB/s", "frac": alg / gpu_s / 1e9 / peak,
                      "traffic": _traffic("profile", N),
-                     "kernel": "profile_count_kernel (+ scan and FFT, all in the interval)",
+                     "kernel": "profile_count_tma_kernel (+ tiles, scan and FFT kernels, all "
+                               "in the interval)",
                      "bytes_per_call": alg, "gpu_ms_per_call": gpu_s * 1e3,
                      "peak_kind": peak_kind},
         "S_k1": float(S[1]),
-        "gpu_launches": steps * (7 + int(L).bit_length() - 1),  # 4 profile + 3 + log2 L FFT kernels
+        "gpu_launches": steps * (3 + _fft_launches(L)),  # count, tiles, scan + the FFT's
         "clocks": clk,
     }
     print(json.dumps(line), flush=True)

@@ -212,10 +212,11 @@ okz_status okz_heights(okz_sim *sim, int64_t y0, int64_t ny, int32_t *out,
 /* Synchronizing. Interface profiles for the power spectrum of Sec. III
  * (Eqs. (15)-(16)): col[x] = sum_y (h(x,y) - H0) and row[y] = sum_x
  * (h(x,y) - H0), x, y = 0 .. L-1, exact int64, into caller-owned host arrays
- * of L values (either may be NULL). Allocates 4 L ceil(L/R) + 28 L bytes
- * (plus 40 L for okz_psd) of stream-ordered device scratch for the call, R
- * being the rows per counting band (16 .. 2048; 2048 at L = 131072, i.e.
- * 35 MiB). Errors: EINVAL, ENOMEM, ECUDA. */
+ * of L values (either may be NULL). Allocates about 4 L ceil(L/R) + 29 L
+ * bytes (plus 40 L for okz_psd) of stream-ordered device scratch for the
+ * call, R being the rows per counting band (a multiple of 16, at most 4080;
+ * 2304 at L = 131072 on a 152-SM GPU, i.e. 32 MiB). Errors: EINVAL, ENOMEM,
+ * ECUDA. */
 okz_status okz_profiles(okz_sim *sim, int64_t *col, int64_t *row);
 
 /* Synchronizing. The power spectrum of Sec. III, Eqs. (15)-(16), on the two

@@ -15,7 +15,10 @@ lattice (d = 2):
   index k standing for the wave number 2 pi k / L.
 
 The column and row profile sums col[x] = sum_y (h[y, x] - c) and
-row[y] = sum_x (h[y, x] - c) are plain sums of the array.
+row[y] = sum_x (h[y, x] - c) are plain sums of the array. On the k axes the
+2-D transform reduces to the 1-D transforms of these sums (the mean only
+enters k = 0), which gives the axis spectrum of large lattices without the
+L x L transform.
 """
 import numpy as np
 
@@ -40,3 +43,15 @@ def psd_axes(h):
     """S_axes[k] = (S(k, 0) + S(0, k)) / 2, k = 0 .. L-1."""
     S = psd_2d(h)
     return 0.5 * (S[0, :] + S[:, 0])
+
+
+def psd_axes_from_profiles(col, row):
+    """S_axes[k] from the profile sums: (|C(k)|^2 + |R(k)|^2) / (2 L^2) for
+    k != 0, C and R the 1-D transforms of col and row (numpy's fft), and
+    S_axes[0] = 0 (the mean is removed). Equal to psd_axes of the heights."""
+    col = np.asarray(col, dtype=np.float64)
+    row = np.asarray(row, dtype=np.float64)
+    L = col.shape[0]
+    S = (np.abs(np.fft.fft(col)) ** 2 + np.abs(np.fft.fft(row)) ** 2) / (2.0 * L * L)
+    S[0] = 0.0
+    return S

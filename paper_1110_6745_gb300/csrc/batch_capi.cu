@@ -458,7 +458,7 @@ okz_status okz_batch_state(okz_batch *b, int32_t slot, uint32_t *planes_out, int
   const size_t out_bytes = (size_t)h.L * (size_t)h.L / 4;
   uint32_t *tmp = nullptr;
   cudaError_t e = cudaStreamSynchronize(b->stream);
-  if (e == cudaSuccess) e = cudaMallocAsync((void **)&tmp, out_bytes, b->stream);
+  if (e == cudaSuccess) e = scratch_alloc((void **)&tmp, out_bytes, b->stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
     set_error("staging allocation for okz_batch_state failed");
@@ -470,7 +470,7 @@ okz_status okz_batch_state(okz_batch *b, int32_t slot, uint32_t *planes_out, int
     e = cudaMemcpyAsync(planes_out, tmp, out_bytes, cudaMemcpyDeviceToHost, b->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(&d, &b->d_slots[slot], sizeof(d), cudaMemcpyDeviceToHost, b->stream);
-  cudaFreeAsync(tmp, b->stream);
+  scratch_free(tmp, b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) return cuda_fail(e, "okz_batch_state");
   if (H0) *H0 = d.H0;

@@ -6,6 +6,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
 
@@ -45,6 +47,44 @@ okz_status cuda_fail(cudaError_t e, const char *what) {
 }
 
 static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// Stream-ordered scratch comes from a memory pool owned by the library, one
+// per device, that keeps up to 1 GiB of freed memory mapped between calls
+// (the default pool returns it to the driver at every synchronization, so
+// each call would map its scratch afresh). Falls back to the default pool if
+// the pool cannot be created.
+static cudaMemPool_t scratch_pool(int dev) {
+  static std::mutex mu;
+  static std::map<int, cudaMemPool_t> pools;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = pools.find(dev);
+  if (it != pools.end()) return it->second;
+  cudaMemPoolProps props;
+  std::memset(&props, 0, sizeof(props));
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = dev;
+  cudaMemPool_t pool = nullptr;
+  if (cudaMemPoolCreate(&pool, &props) == cudaSuccess) {
+    uint64_t keep = 1ull << 30;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  } else {
+    cudaGetLastError();
+    pool = nullptr;
+  }
+  pools[dev] = pool;
+  return pool;
+}
+
+cudaError_t scratch_alloc(void **p, size_t bytes, cudaStream_t st) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  cudaMemPool_t pool = scratch_pool(dev);
+  return pool ? cudaMallocFromPoolAsync(p, bytes, pool, st) : cudaMallocAsync(p, bytes, st);
+}
+
+void scratch_free(void *p, cudaStream_t st) { cudaFreeAsync(p, st); }
 
 Layout layout_for(int64_t L) {
   Layout lay{};
@@ -517,7 +557,7 @@ okz_status okz_heights(okz_sim *sim, int64_t y0, int64_t ny, int32_t *out,
   int32_t *dst = out;
   cudaError_t e;
   if (!out_is_device) {
-    e = cudaMallocAsync((void **)&dst, bytes, sim->stream);
+    e = scratch_alloc((void **)&dst, bytes, sim->stream);
     if (e != cudaSuccess) {
       cudaGetLastError();
       set_error("device staging allocation for heights failed");
@@ -532,7 +572,7 @@ okz_status okz_heights(okz_sim *sim, int64_t y0, int64_t ny, int32_t *out,
                        sim->ctrl, sim->stream);
   if (e == cudaSuccess && !out_is_device)
     e = cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, sim->stream);
-  if (!out_is_device) cudaFreeAsync(dst, sim->stream);
+  if (!out_is_device) scratch_free(dst, sim->stream);
   if (e != cudaSuccess) return cuda_fail(e, "heights");
   e = cudaStreamSynchronize(sim->stream);
   if (e != cudaSuccess) return cuda_fail(e, "heights synchronize");
@@ -554,7 +594,7 @@ static okz_status profiles_and_psd(okz_sim *sim, int64_t *col, int64_t *row, dou
   const size_t vec = ((size_t)L * sizeof(int64_t) + 255) & ~(size_t)255;
   const size_t bytes = scratch + 3 * vec;
   char *buf = nullptr;
-  cudaError_t e = cudaMallocAsync((void **)&buf, bytes, sim->stream);
+  cudaError_t e = scratch_alloc((void **)&buf, bytes, sim->stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
     set_error("device scratch allocation for the profiles failed");
@@ -563,7 +603,7 @@ static okz_status profiles_and_psd(okz_sim *sim, int64_t *col, int64_t *row, dou
   int64_t *dcol = reinterpret_cast<int64_t *>(buf + scratch);
   int64_t *drow = reinterpret_cast<int64_t *>(buf + scratch + vec);
   double *dS = reinterpret_cast<double *>(buf + scratch + 2 * vec);
-  e = launch_profiles(sim->planes[sim->cur], L, sim->parity, sim->hcol, buf, dcol, drow,
+  e = launch_profiles(sim->planes[sim->cur], L, sim->parity, buf, dcol, drow, &sim->ctrl->err,
                       sim->stream);
   if (e == cudaSuccess && fft) e = launch_psd(dcol, drow, L, buf, dS, sim->stream);
   if (e == cudaSuccess && col)
@@ -575,7 +615,7 @@ static okz_status profiles_and_psd(okz_sim *sim, int64_t *col, int64_t *row, dou
   if (e == cudaSuccess && fft)
     e = cudaMemcpyAsync(S, dS, (size_t)L * sizeof(double), cudaMemcpyDeviceToHost,
                         sim->stream);
-  cudaFreeAsync(buf, sim->stream);
+  scratch_free(buf, sim->stream);
   if (e != cudaSuccess) return cuda_fail(e, "profiles");
   return sync_and_check(sim);
 }

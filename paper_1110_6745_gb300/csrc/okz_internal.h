@@ -64,11 +64,16 @@ cudaError_t launch_to_slopes(const uint32_t *B, int64_t L, uint32_t *out, cudaSt
 cudaError_t launch_from_slopes(const uint32_t *slopes, int64_t L, long long H0, int64_t *bcol,
                                uint32_t *B, cudaStream_t st);
 
+// Stream-ordered device scratch from the library's per-device memory pool
+// (capi.cu); freed memory stays mapped for the next call.
+cudaError_t scratch_alloc(void **p, size_t bytes, cudaStream_t st);
+void scratch_free(void *p, cudaStream_t st);
+
 // Interface profiles and power spectrum (psd.cu). Scratch for L: see
 // psd_scratch_bytes; col, row (L int64 each) are device arrays.
 size_t psd_scratch_bytes(int64_t L, bool fft);
-cudaError_t launch_profiles(const uint32_t *planes, int64_t L, bool parity, int64_t *hcol,
-                            void *scratch, int64_t *col, int64_t *row, cudaStream_t st);
+cudaError_t launch_profiles(const uint32_t *planes, int64_t L, bool parity, void *scratch,
+                            int64_t *col, int64_t *row, unsigned int *err, cudaStream_t st);
 // S[k], k = 0..L-1 (device array) from col and row; L a power of two.
 cudaError_t launch_psd(const int64_t *col, const int64_t *row, int64_t L, void *scratch,
                        double *S, cudaStream_t st);

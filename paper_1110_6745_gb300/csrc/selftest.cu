@@ -29,7 +29,7 @@ using namespace okz;
 okz_status okz_selftest_wait_timeout(void *stream) {
   cudaStream_t st = (cudaStream_t)stream;
   unsigned int *err = nullptr;
-  cudaError_t e = cudaMallocAsync((void **)&err, sizeof(unsigned int), st);
+  cudaError_t e = scratch_alloc((void **)&err, sizeof(unsigned int), st);
   if (e != cudaSuccess) {
     cudaGetLastError();
     set_error("okz_selftest_wait_timeout: device allocation failed");
@@ -43,7 +43,7 @@ okz_status okz_selftest_wait_timeout(void *stream) {
   }
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(&h, err, sizeof(unsigned int), cudaMemcpyDeviceToHost, st);
-  cudaFreeAsync(err, st);
+  scratch_free(err, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "okz_selftest_wait_timeout");
   if (h & kErrWaitTimeout) {

@@ -42,6 +42,8 @@ CASES = [  # L, kernel, p, q, sweeps
     (4096, 4, 1.0, 0.0, 12),
     (4096, 2, 0.75, 0.25, 5),
     (8192, 4, 1.0, 1.0, 6),
+    (12288, 2, 0.75, 0.25, 3),  # slope planes; the second 256-word column block half idle
+    (16384, 4, 1.0, 0.0, 4),    # two full column blocks
 ]
 
 
@@ -98,3 +100,73 @@ def test_profiles_sum_to_the_height_sum(okz):
         col, row = sim.profiles()
         H0 = sim.info().H0
     assert int(col.sum()) == int(row.sum()) == S1 - L * L * H0
+
+
+@pytest.mark.parametrize("kernel,p,q", [(4, 0.75, 0.25), (2, 1.0, 0.0)])
+def test_profiles_against_bond_counts_and_heights(okz, kernel, p, q):
+    """L = 2^15 (eight 256-word column blocks, many bands): every step of both
+    profiles equals 2 n - L for the bond counts of the state, the profiles
+    close periodically, col[0] is the sum of column 0's heights (built from
+    its y-bonds, Eq. (3)) and sampled rows match the device heights."""
+    L = 32768
+    with okz.Simulation(L, p, q, seed=9, kernel=kernel) as sim:
+        sim.sweep(6)
+        col, row = sim.profiles()
+        planes, H0, _ = sim.state()
+        rows = {y: sim.heights(y, 1)[0].astype(np.int64) for y in (0, 1, 12345, L - 1)}
+        col0_h = {y: int(sim.heights(y, 1)[0][0]) for y in (5, 20000)}
+    bits = np.unpackbits(planes[0].view(np.uint8), axis=-1, bitorder="little")
+    nX = bits.sum(axis=0, dtype=np.int64)
+    del bits
+    bits = np.unpackbits(planes[1].view(np.uint8), axis=-1, bitorder="little")
+    nY = bits.sum(axis=1, dtype=np.int64)
+    sy0 = 2 * bits[:, 0].astype(np.int64) - 1
+    del bits
+    assert np.array_equal(np.diff(col), 2 * nX[:-1] - L)
+    assert np.array_equal(np.diff(row), 2 * nY[:-1] - L)
+    assert col[-1] + 2 * nX[-1] - L == col[0] and row[-1] + 2 * nY[-1] - L == row[0]
+    h0 = np.concatenate([[0], np.cumsum(sy0)[:-1]])  # h(0, y) - H0
+    assert col[0] == h0.sum()
+    for y, hy in col0_h.items():
+        assert hy - H0 == h0[y]
+    for y, hy in rows.items():
+        assert row[y] == hy.sum() - L * H0
+
+
+@pytest.mark.parametrize("L,kernel,p,q,n", [(8192, 4, 0.75, 0.25, 4), (16384, 4, 1.0, 0.0, 6)])
+def test_psd_large_matches_oracle(okz, orc, L, kernel, p, q, n):
+    """Lattices whose transforms end in radix-4 steps (L = 2^13: one, the
+    last; L = 2^14: a radix-2 stage and one radix-4 step) against the
+    oracle's axis spectrum from its profile sums of the same state."""
+    from oracle import psd
+    with okz.Simulation(L, p, q, seed=5 * L + n, kernel=kernel) as sim:
+        sim.sweep(n)
+        S = sim.psd()
+        h, H0 = _oracle_heights(orc, sim, L, p, q, 5 * L + n)
+    col, row = psd.profile_sums(h, H0)
+    del h
+    ref = psd.psd_axes_from_profiles(col, row)
+    assert S[0] == 0.0
+    assert np.max(np.abs(S - ref)) <= 1e-12 * ref.sum()
+
+
+@pytest.mark.parametrize("L", [32768, 131072])
+def test_psd_parseval_and_sampled_modes(okz, L):
+    """At L = 2^15 and 2^17 (the benchmark's size; radix-4 steps before the
+    last) the spectrum satisfies Parseval's identity with the profiles,
+    sum_k S = (L sum col^2 - (sum col)^2 + L sum row^2 - (sum row)^2) / (2 L^2),
+    and sampled modes equal the explicit sums of Eq. (16) over the profiles."""
+    with okz.Simulation(L, 1.0, 0.0, seed=21) as sim:
+        sim.sweep(40)
+        col, row = sim.profiles()
+        S = sim.psd()
+    c = col.astype(np.float64)
+    r = row.astype(np.float64)
+    tot = (L * np.sum(c * c) - np.sum(c) ** 2 + L * np.sum(r * r) - np.sum(r) ** 2) / (2.0 * L * L)
+    assert S[0] == 0.0
+    assert abs(S.sum() - tot) <= 1e-10 * tot
+    x = np.arange(L)
+    for k in (1, 2, 3, 7, L // 2 - 1, L // 2, L // 2 + 5, L - 1):
+        e = np.exp(-2j * np.pi * ((k * x) % L) / L)
+        Sk = (abs(np.dot(c, e)) ** 2 + abs(np.dot(r, e)) ** 2) / (2.0 * L * L)
+        assert abs(S[k] - Sk) <= 1e-11 * tot, (k, S[k], Sk)

@@ -75,6 +75,10 @@ def test_axis_cut_is_the_transform_of_the_profile_sums(orc):
     tol = 1e-12 * S.sum()
     assert np.allclose(S[0, 1:], Sc[1:], rtol=0, atol=tol)
     assert np.allclose(S[1:, 0], Sr[1:], rtol=0, atol=tol)
+    # the oracle's large-lattice form agrees with the 2-D definition
+    Sa = psd.psd_axes_from_profiles(col, row)
+    assert Sa[0] == 0.0
+    assert np.allclose(Sa, psd.psd_axes(h), rtol=0, atol=tol)
 
 
 def test_profile_sums_by_hand():
