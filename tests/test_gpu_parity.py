@@ -439,7 +439,8 @@ def test_growth_series_L16384_golden(okz):
 # Domain-decomposed random-sequential sweeps (okz_sweep_rs)
 # --------------------------------------------------------------------------
 @pytest.mark.parametrize("L,p,q,seed", [(32, 1.0, 0.0, 1), (64, 0.75, 0.25, 2),
-                                         (128, 1.0, 1.0, 3), (96, 0.5, 0.5, 4)])
+                                         (128, 1.0, 1.0, 3), (96, 0.5, 0.5, 4),
+                                         (320, 0.95, 0.05, 5), (512, 1.0, 0.0, 6)])
 def test_random_sequential_sweeps_match_oracle(okz, orc, L, p, q, seed):
     ref = orc.Sim(L, p, q, seed)
     with okz.Simulation(L, p, q, seed=seed, kernel=okz.OKZ_KERNEL_PARITY_PLAIN) as sim:
