@@ -59,8 +59,8 @@ TRAFFIC = {
                "804ee68040f74f9233afa4baa5220f61551c75144c1729f71dd97aabe8a6d5ba"),
     "ddrs": ((134345472 + 73289472) / 32768 ** 2, "ddrs.cu",
              "6b2f2cbd191834694811fdbf474fc5eb0e73a9edebfc66c6b7baab2356f97324"),
-    "profile": ((537716992 + 3588864) / 65536 ** 2, "psd.cu",
-                "9afb4581b2be7074517c9659a25cb9f6d4c44d90c33260acfc06c55ace912ca6"),
+    "profile": ((546672384 + 8760064) / 65536 ** 2, "psd.cu",
+                "3f9759eae0ced78fce621bcd7e32102d0a5400f4681801d3a991cb01838fd513"),
 }
 
 
@@ -565,12 +565,12 @@ def run_rs(args, world, rank, local):
 
 
 def _fft_launches(L):
-    """Kernels of okz_psd's two transforms: the shared-memory block of the
-    first min(log2 L, 11) stages, a radix-2 stage if an odd number is left,
-    radix-4 steps for the rest (the last also writes S), else a finish."""
+    """Kernels of okz_psd's transform: the shared-memory block of the first
+    min(log2 L, 10) stages, a radix-2 stage if an odd number is left, radix-4
+    steps for the rest, and the finish that writes S."""
     lg = int(L).bit_length() - 1
-    rem = lg - min(lg, 11)
-    return 1 + rem % 2 + rem // 2 + (1 if rem < 2 else 0)
+    rem = lg - min(lg, 10)
+    return 1 + rem % 2 + rem // 2 + 1
 
 
 def run_spectrum(args, world, rank, local):

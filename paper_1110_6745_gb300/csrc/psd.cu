@@ -88,7 +88,7 @@ PsdLayout psd_layout(int64_t L, bool fft) {
   s.cntY = take(off, (size_t)L * sizeof(uint32_t) + 2 * sizeof(long long));
   s.tiles = take(off, 2 * (size_t)n_tiles(L) * sizeof(long long));
   if (fft) {
-    s.a = take(off, 2 * (size_t)L * sizeof(double2));
+    s.a = take(off, (size_t)L * sizeof(double2));
     s.tw = take(off, (size_t)(L / 2) * sizeof(double2));
   }
   s.total = off;
@@ -164,15 +164,18 @@ __device__ __forceinline__ void red_add_if(bool p, uint32_t *addr, uint32_t v) {
       : "memory");
 }
 
-// Row counts of a group: two rows per warp sum (each half at most 1024), one
-// shared-memory reduction per pair (each half at most 8192 per block).
+// Row counts of a group: two rows per warp sum (each half at most 1024);
+// lane j < 8 keeps the sum of pair j and the eight add it to their rows'
+// shared counters in one reduction (each half at most 8192 per block).
 __device__ __forceinline__ void add_rows(const uint32_t yw[kGroup], uint32_t *acc, int lane) {
+  uint32_t mine = 0;
 #pragma unroll
   for (int k = 0; k < kGroup; k += 2) {
     const uint32_t v = (uint32_t)__popc(yw[k]) | ((uint32_t)__popc(yw[k + 1]) << 16);
     const uint32_t s = __reduce_add_sync(0xFFFFFFFFu, v);
-    red_add_if(lane == 0, &acc[k >> 1], s);
+    mine = (lane == (k >> 1)) ? s : mine;
   }
+  red_add_if(lane < kGroup / 2, &acc[lane & (kGroup / 2 - 1)], mine);
 }
 
 // The block's row counts to cntY, its column counts (word column w) to band
@@ -364,8 +367,12 @@ profile_count_tma_kernel(const uint32_t *__restrict__ P, int L, int R,
         const uint32_t *src = P + (size_t)(row < L ? row : row - L) * W;
         uint32_t *dst = ring + ((size_t)st * kSlotRows + lane) * kSlotWords;
         tma::fence_proxy_async();
-        tma::load_1d(dst, src + s0, segb, &full[st]);
-        tma::load_1d(dst + segw, src + tailw, 16u, &full[st]);
+        if (tailw != 0) {  // the 4 words after the segment follow it in memory
+          tma::load_1d(dst, src + s0, segb + 16u, &full[st]);
+        } else {           // the row's last block: they are its first 4 words
+          tma::load_1d(dst, src + s0, segb, &full[st]);
+          tma::load_1d(dst + segw, src, 16u, &full[st]);
+        }
       }
       issued = g + 1;
     }
@@ -476,7 +483,7 @@ profile_scan_kernel(const uint32_t *__restrict__ cntX, const uint32_t *__restric
   if (i < L) (blockIdx.y ? row : col)[i] = (int64_t)(off + sh[warp] + pw);
 }
 
-constexpr int kFftLogBlock = 11;  // points per shared-memory FFT block: 2048
+constexpr int kFftLogBlock = 10;  // points per shared-memory FFT block: 1024
 
 // u, x <- u + w x, u - w x with the rounding of every step fixed, so that all
 // FFT kernels compute a butterfly alike.
@@ -492,13 +499,15 @@ __device__ __forceinline__ double power(double2 c) {
   return __fma_rn(c.x, c.x, __dmul_rn(c.y, c.y));
 }
 
-// The radix-2 decimation-in-time FFT of transform t = blockIdx.y (t = 0: col,
-// 1: row) on the bit-reversed input a_t[p] = src[bitrev(p)]. Its first lb
-// stages (half-lengths 1 .. 2^(lb-1)) never leave a block of B = 2^lb points:
-// block b loads points b B .. b B + B - 1, runs them in shared memory with
-// twiddles e^{-2 pi i k / B}, and writes them to a; if L > B, the blocks of
-// transform 0 also write their slice of the table tw[j] = e^{-2 pi i j / L},
-// j < L/2, for the later stages.
+// The radix-2 decimation-in-time FFT of z = col + i row, on the bit-reversed
+// input a[p] = z[bitrev(p)]; one transform gives both axes, since with
+// Z = FFT(z) the transforms of the real col and row satisfy
+// |C(k)|^2 + |R(k)|^2 = (|Z(k)|^2 + |Z(L-k)|^2) / 2. The first lb stages
+// (half-lengths 1 .. 2^(lb-1)) never leave a block of B = 2^lb points: block
+// b loads points b B .. b B + B - 1, runs them in shared memory with
+// twiddles e^{-2 pi i k / B}, and writes them to a; if L > B, the blocks also
+// write their slice of the table tw[j] = e^{-2 pi i j / L}, j < L/2, for the
+// later stages.
 __global__ void __launch_bounds__(1 << (kFftLogBlock - 1))
 fft_block_kernel(const int64_t *__restrict__ col, const int64_t *__restrict__ row, int64_t L,
                  int lg, int lb, double2 *__restrict__ a, double2 *__restrict__ tw) {
@@ -506,17 +515,16 @@ fft_block_kernel(const int64_t *__restrict__ col, const int64_t *__restrict__ ro
   __shared__ double2 wb[1 << (kFftLogBlock - 1)];
   const int B = 1 << lb, t = threadIdx.x, nt = blockDim.x;
   const int64_t base = (int64_t)blockIdx.x * B;
-  const int64_t *src = blockIdx.y ? row : col;
   for (int i = t; i < B; i += nt) {
     const uint32_t r = __brev((uint32_t)(base + i)) >> (32 - lg);
-    v[i] = make_double2((double)src[r], 0.0);
+    v[i] = make_double2((double)col[r], (double)row[r]);
   }
   for (int k = t; k < B / 2; k += nt) {
     double sn, cs;
     sincospi(-2.0 * (double)k / (double)B, &sn, &cs);
     wb[k] = make_double2(cs, sn);
   }
-  if (blockIdx.y == 0 && L > B) {
+  if (L > B) {
     const int64_t per = (L / 2) / gridDim.x;
     for (int64_t k = t; k < per; k += nt) {
       const int64_t j = (int64_t)blockIdx.x * per + k;
@@ -538,39 +546,31 @@ fft_block_kernel(const int64_t *__restrict__ col, const int64_t *__restrict__ ro
     }
     __syncthreads();
   }
-  double2 *dst = a + (int64_t)blockIdx.y * L + base;
+  double2 *dst = a + base;
   for (int i = t; i < B; i += nt) dst[i] = v[i];
 }
 
-// One radix-2 stage with half-length 2^lh, both transforms (blockIdx.y).
+// One radix-2 stage with half-length 2^lh.
 __global__ void __launch_bounds__(256)
 fft_stage_kernel(double2 *__restrict__ a, const double2 *__restrict__ tw, int64_t L, int lh,
                  int lg) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= L / 2) return;
-  double2 *v = a + blockIdx.y * L;
   const int64_t half = 1LL << lh;
   const int64_t j = i & (half - 1);
   const int64_t p = ((i >> lh) << (lh + 1)) | j;
-  double2 u = v[p], x = v[p + half];
+  double2 u = a[p], x = a[p + half];
   bfly(u, x, tw[j << (lg - 1 - lh)]);
-  v[p] = u;
-  v[p + half] = x;
+  a[p] = u;
+  a[p + half] = x;
 }
 
-// S[k] = (|h(k,0)|^2 + |h(0,k)|^2) / 2 with h = (transform) / L, S[0] = 0.
-__device__ __forceinline__ void write_psd(double *S, int64_t k, double2 c, double2 r, double inv) {
-  S[k] = (k == 0) ? 0.0 : __dmul_rn(__dadd_rn(power(c), power(r)), inv);
-}
-
-// Stages lh and lh+1 (half-lengths h = 2^lh and 2h) of both transforms as
-// radix-4 steps: thread i takes the points p + {0, h, 2h, 3h}, p = its 4h
-// group's start + j (j < h), and runs the four radix-2 butterflies of the two
-// stages on them. With FINISH (the last two stages) it writes S instead.
-template <bool FINISH>
+// Stages lh and lh+1 (half-lengths h = 2^lh and 2h) as radix-4 steps: thread
+// i takes the points p + {0, h, 2h, 3h}, p = its 4h group's start + j
+// (j < h), and runs the four radix-2 butterflies of the two stages on them.
 __global__ void __launch_bounds__(256)
 fft_radix4_kernel(double2 *__restrict__ a, const double2 *__restrict__ tw, int64_t L, int lh,
-                  int lg, double *__restrict__ S) {
+                  int lg) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= L / 4) return;
   const int64_t h = 1LL << lh;
@@ -579,33 +579,32 @@ fft_radix4_kernel(double2 *__restrict__ a, const double2 *__restrict__ tw, int64
   const double2 w1 = tw[j << (lg - 1 - lh)];
   const double2 w2a = tw[j << (lg - 2 - lh)];
   const double2 w2b = tw[(j + h) << (lg - 2 - lh)];
-  double2 x[2][4];
+  double2 x[4];
 #pragma unroll
-  for (int t = 0; t < 2; ++t) {
-    double2 *v = a + t * L;
+  for (int q = 0; q < 4; ++q) x[q] = a[p + q * h];
+  bfly(x[0], x[1], w1);
+  bfly(x[2], x[3], w1);
+  bfly(x[0], x[2], w2a);
+  bfly(x[1], x[3], w2b);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) x[t][q] = v[p + q * h];
-    bfly(x[t][0], x[t][1], w1);
-    bfly(x[t][2], x[t][3], w1);
-    bfly(x[t][0], x[t][2], w2a);
-    bfly(x[t][1], x[t][3], w2b);
-    if (!FINISH) {
-#pragma unroll
-      for (int q = 0; q < 4; ++q) v[p + q * h] = x[t][q];
-    }
-  }
-  if (FINISH) {
-    const double inv = 1.0 / (2.0 * (double)L * (double)L);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) write_psd(S, p + q * h, x[0][q], x[1][q], inv);
-  }
+  for (int q = 0; q < 4; ++q) a[p + q * h] = x[q];
 }
 
+// S[k] = S[L-k] = (|Z(k)|^2 + |Z(L-k)|^2) / (4 L^2) (the axis average of
+// |h(k,0)|^2 and |h(0,k)|^2 with h = transform / L), S[0] = 0: thread k
+// writes both entries of the pair k, L-k.
 __global__ void __launch_bounds__(256)
 psd_finish_kernel(const double2 *__restrict__ a, int64_t L, double *__restrict__ S) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= L) return;
-  write_psd(S, k, a[k], a[L + k], 1.0 / (2.0 * (double)L * (double)L));
+  if (k > L / 2) return;
+  if (k == 0) {
+    S[0] = 0.0;
+    return;
+  }
+  const double v = __dmul_rn(__dadd_rn(power(a[k]), power(a[L - k])),
+                             1.0 / (4.0 * (double)L * (double)L));
+  S[k] = v;
+  S[L - k] = v;
 }
 
 size_t psd_scratch_bytes(int64_t L, bool fft) { return psd_layout(L, fft).total; }
@@ -659,24 +658,16 @@ cudaError_t launch_psd(const int64_t *col, const int64_t *row, int64_t L, void *
   while ((1LL << lg) < L) ++lg;
   const int lb = lg < kFftLogBlock ? lg : kFftLogBlock;
   const int B = 1 << lb;
-  fft_block_kernel<<<dim3((unsigned)(L / B), 2), B / 2 > 0 ? B / 2 : 1, 0, st>>>(col, row, L, lg,
-                                                                                  lb, a, tw);
+  fft_block_kernel<<<(unsigned)(L / B), B / 2 > 0 ? B / 2 : 1, 0, st>>>(col, row, L, lg, lb, a,
+                                                                         tw);
   int lh = lb;
   if ((lg - lh) % 2 == 1) {  // an odd number of stages left: one radix-2 stage first
-    fft_stage_kernel<<<dim3((unsigned)((L / 2 + 255) / 256), 2), 256, 0, st>>>(a, tw, L, lh, lg);
+    fft_stage_kernel<<<(unsigned)((L / 2 + 255) / 256), 256, 0, st>>>(a, tw, L, lh, lg);
     ++lh;
   }
-  const unsigned g4 = (unsigned)((L / 4 + 255) / 256);
-  bool done = false;
-  for (; lh < lg; lh += 2) {
-    if (lh + 2 == lg) {
-      fft_radix4_kernel<true><<<g4, 256, 0, st>>>(a, tw, L, lh, lg, S);
-      done = true;
-    } else {
-      fft_radix4_kernel<false><<<g4, 256, 0, st>>>(a, tw, L, lh, lg, S);
-    }
-  }
-  if (!done) psd_finish_kernel<<<(unsigned)((L + 255) / 256), 256, 0, st>>>(a, L, S);
+  for (; lh < lg; lh += 2)
+    fft_radix4_kernel<<<(unsigned)((L / 4 + 255) / 256), 256, 0, st>>>(a, tw, L, lh, lg);
+  psd_finish_kernel<<<(unsigned)((L / 2 + 1 + 255) / 256), 256, 0, st>>>(a, L, S);
   return cudaGetLastError();
 }
 

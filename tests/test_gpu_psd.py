@@ -135,9 +135,10 @@ def test_profiles_against_bond_counts_and_heights(okz, kernel, p, q):
 
 @pytest.mark.parametrize("L,kernel,p,q,n", [(8192, 4, 0.75, 0.25, 4), (16384, 4, 1.0, 0.0, 6)])
 def test_psd_large_matches_oracle(okz, orc, L, kernel, p, q, n):
-    """Lattices whose transforms end in radix-4 steps (L = 2^13: one, the
-    last; L = 2^14: a radix-2 stage and one radix-4 step) against the
-    oracle's axis spectrum from its profile sums of the same state."""
+    """Lattices whose transforms go on past the shared-memory block (L = 2^13:
+    a radix-2 stage and a radix-4 step; L = 2^14: two radix-4 steps)
+    against the oracle's axis spectrum from its profile sums of the same
+    state."""
     from oracle import psd
     with okz.Simulation(L, p, q, seed=5 * L + n, kernel=kernel) as sim:
         sim.sweep(n)
