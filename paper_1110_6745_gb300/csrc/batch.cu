@@ -102,10 +102,18 @@ __device__ __forceinline__ void group_update(uint32_t *B, int L, int W, uint32_t
   }
 }
 
+// Level 0 of a group is the same in both half-sweeps of a sweep (a site is
+// active in one of them). CACHE = 1: keep the level-0 words drawn in the
+// first half-sweep in cw and mark bit cbit of cvalid; CACHE = 2: take them
+// from there in the second (draw them if the first did not).
+constexpr int kCacheGroups = 8;  // groups per thread up to which level 0 is kept
+
 // Acceptance of 4 words (lazy, bit-sliced U < P / U < Q) -> flips.
+template <int CACHE>
 __device__ __forceinline__ void accept4(const uint32_t mn[4], const uint32_t mx[4], uint32_t g,
                                         uint32_t t, const uint32_t *rks, const Accept &acc,
-                                        uint32_t f[4]) {
+                                        uint32_t f[4], uint32_t *cw, uint32_t &cvalid,
+                                        uint32_t cbit) {
   const uint64_t full = 1ull << acc.k;
   uint32_t ltp[4], eqp[4], ltq[4], eqq[4];
 #pragma unroll
@@ -118,7 +126,18 @@ __device__ __forceinline__ void accept4(const uint32_t mn[4], const uint32_t mx[
   for (int m = 0; m < acc.k; ++m) {
     if (((eqp[0] | eqq[0]) | (eqp[1] | eqq[1]) | (eqp[2] | eqq[2]) | (eqp[3] | eqq[3])) == 0u)
       break;
-    const u32x4 rb = philox10_sm(g, 0u, t, (uint32_t)m, rks);
+    u32x4 rb;
+    if (CACHE == 2 && m == 0 && (cvalid & cbit)) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) rb.v[j] = cw[j];
+    } else {
+      rb = philox10_sm(g, 0u, t, (uint32_t)m, rks);
+      if (CACHE == 1 && m == 0) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) cw[j] = rb.v[j];
+        cvalid |= cbit;
+      }
+    }
     const uint32_t pb = (uint32_t)(acc.P >> (acc.k - 1 - m)) & 1u;
     const uint32_t qb = (uint32_t)(acc.Q >> (acc.k - 1 - m)) & 1u;
 #pragma unroll
@@ -135,11 +154,12 @@ __device__ __forceinline__ void accept4(const uint32_t mn[4], const uint32_t mx[
 // row below, row above), 2 neighbour words, 1 vector store. Whole-word
 // stores are safe: every bit another thread reads from these words sits on a
 // site this half-sweep does not move.
-template <bool POW2, int SP>
+template <bool POW2, int SP, int CACHE>
 __device__ __forceinline__ void row_group_update(uint32_t *B, int L, int W, uint32_t gpr,
                                                  int lg_gpr, uint32_t g, uint32_t t,
                                                  const uint32_t *rks, const Accept &acc,
-                                                 int &dH0) {
+                                                 int &dH0, uint32_t *cw, uint32_t &cvalid,
+                                                 uint32_t cbit) {
   constexpr int s = SP;
   const uint32_t y = POW2 ? (g >> lg_gpr) : (g / gpr);
   const uint32_t w0 = 4 * (g - y * gpr);
@@ -168,7 +188,7 @@ __device__ __forceinline__ void row_group_update(uint32_t *B, int L, int W, uint
     mx[j] = lop3<0x80>(lop3<kMax>(l, r, c[j]), lop3<kMax>(d[j], u[j], c[j]), a);
   }
   uint32_t f[4];
-  accept4(mn, mx, g, t, rks, acc, f);
+  accept4<CACHE>(mn, mx, g, t, rks, acc, f, cw, cvalid, cbit);
   if ((f[0] | f[1] | f[2] | f[3]) != 0u)
     *(uint4 *)(row + w0) = make_uint4(c[0] ^ f[0], c[1] ^ f[1], c[2] ^ f[2], c[3] ^ f[3]);
   if (g == 0 && (f[0] & 1u)) dH0 += (mn[0] & 1u) ? 2 : -2;  // site (0,0)
@@ -183,20 +203,35 @@ __device__ __forceinline__ void cta_sweeps(uint32_t *B, int L, uint32_t t0, int 
     const uint32_t gpr = (uint32_t)W / 4;
     const bool pow2 = (gpr & (gpr - 1)) == 0;
     const int lg = __ffs(gpr) - 1;
+    // a thread takes the same groups in both half-sweeps; with at most
+    // kCacheGroups of them it keeps their level-0 words between the two
+    const bool cache = groups <= kCacheGroups * blockDim.x;
+    uint32_t cw[4 * kCacheGroups];
     for (int i = 0; i < n; ++i) {
       const uint32_t t = t0 + (uint32_t)i;
-      if (pow2) {
+      uint32_t cvalid = 0;
+      if (cache && pow2) {
+        uint32_t q = 0;
+        for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x, ++q)
+          row_group_update<true, 0, 1>(B, L, W, gpr, lg, g, t, rks, acc, dH0, cw + 4 * q, cvalid,
+                                       1u << q);
+        __syncthreads();
+        q = 0;
+        for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x, ++q)
+          row_group_update<true, 1, 2>(B, L, W, gpr, lg, g, t, rks, acc, dH0, cw + 4 * q, cvalid,
+                                       1u << q);
+      } else if (pow2) {
         for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x)
-          row_group_update<true, 0>(B, L, W, gpr, lg, g, t, rks, acc, dH0);
+          row_group_update<true, 0, 0>(B, L, W, gpr, lg, g, t, rks, acc, dH0, cw, cvalid, 0u);
         __syncthreads();
         for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x)
-          row_group_update<true, 1>(B, L, W, gpr, lg, g, t, rks, acc, dH0);
+          row_group_update<true, 1, 0>(B, L, W, gpr, lg, g, t, rks, acc, dH0, cw, cvalid, 0u);
       } else {
         for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x)
-          row_group_update<false, 0>(B, L, W, gpr, lg, g, t, rks, acc, dH0);
+          row_group_update<false, 0, 0>(B, L, W, gpr, lg, g, t, rks, acc, dH0, cw, cvalid, 0u);
         __syncthreads();
         for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x)
-          row_group_update<false, 1>(B, L, W, gpr, lg, g, t, rks, acc, dH0);
+          row_group_update<false, 1, 0>(B, L, W, gpr, lg, g, t, rks, acc, dH0, cw, cvalid, 0u);
       }
       __syncthreads();
     }
