@@ -205,7 +205,9 @@ __device__ __forceinline__ void cta_sweeps(uint32_t *B, int L, uint32_t t0, int 
     const int lg = __ffs(gpr) - 1;
     // a thread takes the same groups in both half-sweeps; with at most
     // kCacheGroups of them it keeps their level-0 words between the two
-    const bool cache = groups <= kCacheGroups * blockDim.x;
+    // (with k >= 3 the later levels dominate and the local-memory round trip
+    // does not pay: -1.5 % on a k = 32 mix, +6 % at k = 1)
+    const bool cache = acc.k <= 2 && groups <= kCacheGroups * blockDim.x;
     uint32_t cw[4 * kCacheGroups];
     for (int i = 0; i < n; ++i) {
       const uint32_t t = t0 + (uint32_t)i;
