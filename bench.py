@@ -57,8 +57,8 @@ N_SMS = 152
 TRAFFIC = {
     "parity": ((556869376 + 485988608) / 65536 ** 2, "parity.cu",
                "804ee68040f74f9233afa4baa5220f61551c75144c1729f71dd97aabe8a6d5ba"),
-    "ddrs": ((134345472 + 73289472) / 32768 ** 2, "ddrs.cu",
-             "6b2f2cbd191834694811fdbf474fc5eb0e73a9edebfc66c6b7baab2356f97324"),
+    "ddrs": ((134544640 + 73219072) / 32768 ** 2, "ddrs.cu",
+             "c2f242e7e5e1b6fc82f8f918aac71218c2f2182050306070f95ae2ed2e30a831"),
     "profile": ((546672384 + 8760064) / 65536 ** 2, "psd.cu",
                 "3f9759eae0ced78fce621bcd7e32102d0a5400f4681801d3a991cb01838fd513"),
 }

@@ -48,9 +48,10 @@ ddrs_kernel(uint32_t *__restrict__ B, int L, uint32_t t, const RoundKeys rk, uin
     cell[ly] = __funnelshift_r(a, b, sh);
     if (ly < kCell) next_col |= ((b >> sh) & 1u) << ly;
   }
-  // loop invariants: p(x,y) = (x0 + lx + y0 + ly) mod 2 (L is even), and the
+  // loop invariants: the sites of parity (x0 + lx + y0 + ly) mod 2 = 1 (L is
+  // even) are pm0 in rows of even ly and its complement in odd rows, and the
   // local coordinates of site (0,0) if this cell holds it (else 64)
-  const uint32_t pbase = (uint32_t)(x0 + y0) & 1u;
+  const uint32_t pm0 = ((uint32_t)(x0 + y0) & 1u) ? 0x55555555u : 0xAAAAAAAAu;
   const int lx00 = (L - x0) % L < kCell ? (L - x0) % L : 64;
   const int ly00 = (L - y0) % L < kCell ? (L - y0) % L : 64;
   const bool p_on = pq_on & 1u, q_on = pq_on & 2u;
@@ -72,15 +73,18 @@ ddrs_kernel(uint32_t *__restrict__ B, int L, uint32_t t, const RoundKeys rk, uin
     const int lx = (int)(first & (kCell - 1)), ly = (int)((first >> 16) & (kCell - 1));
     if (lx == 0 || ly == 0) continue;  // dead border
     const uint32_t row = cell[ly];
-    // bits 0, 1, 2 = left neighbour, own site, right neighbour
-    const uint32_t hi = (next_col >> ly) & 1u;
-    const uint32_t w3 = __funnelshift_r(row, hi, lx - 1);
-    const uint32_t cc = ((w3 >> 1) ^ (uint32_t)(lx + ly) ^ pbase) & 1u;  // own bit ^ parity
-    const uint32_t dn = (cell[ly - 1] >> lx) & 1u, up = (cell[ly + 1] >> lx) & 1u;
-    const uint32_t s4 = (w3 & 1u) + ((w3 >> 2) & 1u) + dn + up;  // neighbours with bit 1
-    // a minimum has all four neighbours equal to cc, a maximum all four unequal
-    const bool all1 = s4 == 4u, all0 = s4 == 0u;
-    const bool is_min = cc ? all1 : all0, is_max = cc ? all0 : all1;
+    // the whole row at once: bit lx of l / r is the left / right neighbour
+    // (bit 31 of r: the next cell's column), then three-input truth tables
+    // for "all four neighbours equal the own bit" (E) and "all four differ"
+    // (N); a site of parity 0 is a minimum iff E and a maximum iff N,
+    // parity 1 the reverse
+    const uint32_t l = row << 1, r = __funnelshift_r(row, next_col >> ly, 1);
+    const uint32_t dn = cell[ly - 1], up = cell[ly + 1];
+    const uint32_t E = lop3<0x81>(l, r, row) & lop3<0x81>(dn, up, row);
+    const uint32_t N = lop3<0x42>(l, r, row) & lop3<0x42>(dn, up, row);
+    const uint32_t pm = (ly & 1) ? ~pm0 : pm0, m = 1u << lx;
+    const bool is_min = (lop3<0xCA>(pm, N, E) & m) != 0u;  // pm ? N : E
+    const bool is_max = (lop3<0xCA>(pm, E, N) & m) != 0u;
     const bool accept = (is_min && p_on && u <= Pm1) || (is_max && q_on && u <= Qm1);
     if (!accept) continue;
     cell[ly] = row ^ (1u << lx);
