@@ -216,7 +216,8 @@ okz_status okz_heights(okz_sim *sim, int64_t y0, int64_t ny, int32_t *out,
  * bytes (plus 40 L for okz_psd) of stream-ordered device scratch for the
  * call, R being the rows per counting band (a multiple of 16, at most 4080;
  * 2304 at L = 131072 on a 152-SM GPU, i.e. 32 MiB). Errors: EINVAL, ENOMEM,
- * ECUDA. */
+ * ECUDA, ETIMEOUT (a bounded wait of the streaming counting kernel gave up;
+ * the outputs are then undefined). */
 okz_status okz_profiles(okz_sim *sim, int64_t *col, int64_t *row);
 
 /* Synchronizing. The power spectrum of Sec. III, Eqs. (15)-(16), on the two
@@ -225,9 +226,11 @@ okz_status okz_profiles(okz_sim *sim, int64_t *col, int64_t *row);
  *   h(k,0) = (1/L) sum_{x,y} (h(x,y) - <h>) e^{-2 pi i k x / L},
  * (the d = 2 normalisation L^{-d/2}; S[0] = 0 as the mean is removed; the
  * sign of the exponent does not change |h(k)|). Computed from the exact
- * profiles (okz_profiles) by radix-2 FFTs in fp64 on the device. S is a
+ * profiles (okz_profiles) by one fp64 FFT of col + i row on the device
+ * (radix-2 decimation in time; S is symmetric, S[k] = S[L-k]). S is a
  * caller-owned host array of L doubles. Needs a power-of-two L (EUNSUPPORTED
- * otherwise). Errors: EINVAL, EUNSUPPORTED, ENOMEM, ECUDA. */
+ * otherwise). Errors: EINVAL, EUNSUPPORTED, ENOMEM, ECUDA, ETIMEOUT (as
+ * okz_profiles). */
 okz_status okz_psd(okz_sim *sim, double *S);
 
 /* Synchronizing. Copies the state buffer (X plane then Y plane, layout
