@@ -451,9 +451,11 @@ ORC_API void orc_window_sweeps(int64_t L, int64_t x0, int64_t y0, int64_t w, int
     for (int64_t it = 0; it < n; ++it) {
         uint64_t t = t0 + (uint64_t)it;
         for (int s = 0; s < 2; ++s) {
-            draw_cache cache;
-            draw_cache_init(&cache, seed, t, L);
-            for (int64_t j = 1; j < h; ++j)
+            /* rows of one half-sweep touch disjoint bonds (as in halfsweep_rows) */
+#pragma omp parallel for schedule(static) if (w * h >= 4096)
+            for (int64_t j = 1; j < h; ++j) {
+                draw_cache cache;
+                draw_cache_init(&cache, seed, t, L);
                 for (int64_t i = 1; i < w; ++i) {
                     int64_t gx = (x0 + i) % L, gy = (y0 + j) % L;
                     if ((gx + gy) % 2 != s)
@@ -472,6 +474,7 @@ ORC_API void orc_window_sweeps(int64_t L, int64_t x0, int64_t y0, int64_t w, int
                         *up ^= 1;
                     }
                 }
+            }
         }
     }
 }

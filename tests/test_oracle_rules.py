@@ -255,6 +255,66 @@ def test_random_sequential_variant(orc):
     _check_invariants(sim)
 
 
+def _p32(p):
+    """round-half-even(p * 2^32) from the exact rational value of the double p."""
+    return round(Fraction(p) * 2 ** 32)
+
+
+@pytest.mark.parametrize("p", [0.0, 1.0, 0.5, 0.75, 0.25, 2.0 ** -32,  # dyadic
+                               0.1, 0.95, 0.05, 1.0 / 3.0, 0.3141592653589793,  # rounded
+                               2.0 ** -33, 3 * 2.0 ** -33, 5 * 2.0 ** -33,  # exactly half-way
+                               1.0 - 2.0 ** -33, 0.5 + 2.0 ** -33])
+def test_rs_threshold_rounds_half_to_even(orc, p):
+    """The 32-bit threshold of the random-sequential rule is p * 2^32 rounded to
+    the nearest integer, ties to even (2^-33 -> 0, 3*2^-33 -> 2, 5*2^-33 -> 2),
+    against Python's exact Fraction arithmetic."""
+    want = _p32(p)
+    assert orc.rs_threshold(p) == want
+    if p == 5 * 2.0 ** -33:
+        assert want == 2
+    if p == 3 * 2.0 ** -33:
+        assert want == 2
+
+
+def _rs_by_hand(orc, h, L, p, q, seed, t):
+    """One random-sequential sweep on a height array, written from the rule:
+    attempt a = 0 .. L*L-1 in order draws Philox4x32-10 at counter
+    (a mod 2^32, a div 2^32, t, 256), picks x = floor(r0 * L / 2^32),
+    y = floor(r1 * L / 2^32), and moves a minimum up (maximum down) by 2 when
+    r2 is below the 32-bit threshold of p (of q)."""
+    P32, Q32 = _p32(p), _p32(q)
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    sites = []
+    for a in range(L * L):
+        r = orc.philox4x32_10([a & 0xFFFFFFFF, a >> 32, t, 256], key)
+        x, y = (int(r[0]) * L) >> 32, (int(r[1]) * L) >> 32
+        sites.append((x, y))
+        nb = [h[y, (x - 1) % L], h[y, (x + 1) % L], h[(y - 1) % L, x], h[(y + 1) % L, x]]
+        if all(v == h[y, x] + 1 for v in nb) and int(r[2]) < P32:
+            h[y, x] += 2
+        elif all(v == h[y, x] - 1 for v in nb) and int(r[2]) < Q32:
+            h[y, x] -= 2
+    return h, sites
+
+
+@pytest.mark.parametrize("L,p,q,seed", [(2, 1.0, 1.0, 17), (4, 1.0, 0.0, 3), (6, 0.75, 0.25, 4),
+                                         (8, 0.5, 0.5, 5), (10, 1.0, 1.0, 6)])
+def test_random_sequential_sweep_by_hand(orc, L, p, q, seed):
+    """orc_rs_sweeps equals the rule applied attempt by attempt to a height
+    array in Python (site decode by multiply-high, strict threshold compare),
+    over three sweeps, for power-of-two and other even L (on the 2 x 2 torus
+    every site starts as an extremum, so with p = q = 1 the first attempt
+    always moves its decoded site); the picked sites stay in [0, L)."""
+    sim = orc.Sim(L, p, q, seed)
+    h = sim.heights()
+    for t in range(3):
+        sim.rs_sweep(1)
+        h, sites = _rs_by_hand(orc, h, L, p, q, seed, t)
+        assert np.array_equal(sim.heights(), h), (L, t)
+        xs, ys = zip(*sites)
+        assert min(xs) >= 0 and max(xs) < L and min(ys) >= 0 and max(ys) < L
+
+
 def test_domain_decomposed_random_sequential(orc):
     """The blocked random-sequential dynamics keeps every height-function
     invariant; every move changes a height by 2, and with p = 1, q = 0 the
@@ -311,3 +371,30 @@ def test_domain_decomposed_cells_are_independent(orc):
             h = _ddrs_by_hand(orc, h, L, C, 0.75, 0.25, seed, t,
                               reversed(range((L // C) ** 2)))
             assert np.array_equal(sim.heights(), h), (L, C, t)
+
+
+@pytest.mark.parametrize("L,p,q,s_sel,n", [(64, 1.0, 0.0, 0.5, 6), (96, 0.75, 0.25, 0.5, 5),
+                                           (64, 1.0, 1.0, 0.5, 7), (128, 0.95, 0.05, 0.5, 4)])
+def test_window_mode_matches_full_lattice(orc, L, p, q, s_sel, n):
+    """The light-cone window simulation (used to check the largest lattices
+    site by site) reproduces the full-lattice oracle on every site farther
+    than 2n + 1 from the window's edges, for windows inside the lattice,
+    across the periodic wrap in x, in y and at the corner, and one covering
+    more than the whole lattice; sites near the window edges are allowed to
+    differ (and do, somewhere, for the last one)."""
+    ref = orc.Sim(L, p, q, 23, s_sel=s_sel)
+    ref.sweep(n)
+    m = 2 * n + 2
+    for (x0, y0, w, h) in [(5, 9, 2 * m + 20, 2 * m + 11), (L - m - 3, 17, 2 * m + 9, 2 * m + 4),
+                           (3, L - m - 6, 2 * m + 8, 2 * m + 12),
+                           (L - m - 2, L - m - 5, 2 * m + 7, 2 * m + 10),
+                           (L - 7, L - 3, L + 2 * m, L + 2 * m)]:
+        WX, WY = orc.window_flat_sweeps(L, x0, y0, w, h, p, q, 23, n, s_sel=s_sel)
+        ys = (np.arange(h) + y0) % L
+        xs = (np.arange(w) + x0) % L
+        RX = ref.X[np.ix_(ys, xs)]
+        RY = ref.Y[np.ix_(ys, xs)]
+        assert np.array_equal(WX[m:h - m, m:w - m], RX[m:h - m, m:w - m]), (x0, y0)
+        assert np.array_equal(WY[m:h - m, m:w - m], RY[m:h - m, m:w - m]), (x0, y0)
+    # the frozen edges of the window are not the lattice's (the margin matters)
+    assert not (np.array_equal(WX, RX) and np.array_equal(WY, RY))
