@@ -282,14 +282,15 @@ okz_status okz_selftest_wait_timeout(void *stream);
  * allocating after start-up.
  *
  * Computes the same exact sums and W^2 as okz_width2 for a state the caller
- * owns: `planes` is a device pointer to the slope-plane layout above (X
- * plane then Y plane), `H0` its h(0,0), `stream` the cudaStream_t to run on
+ * owns: `planes` is a 16-byte aligned device pointer to the slope-plane
+ * layout above (X plane then Y plane; an unaligned pointer is rejected with
+ * OKZ_EINVAL before any kernel runs), `H0` its h(0,0), `stream` the cudaStream_t to run on
  * (NULL = the legacy default stream). 32 <= L <= 131072 and L % 32 == 0;
  * a larger L is rejected with OKZ_EINVAL ("exceeds the fixed scratch size").
  * Outputs as okz_width2; any may be NULL. Synchronizing: waits for `stream`.
  *
  * It allocates nothing (no cudaMalloc, cudaFree or pinned buffers). Its
- * scratch is one fixed device array of 1 MiB + 129 KiB + 256 B, present on
+ * scratch is one fixed device array of 1 MiB + 128 KiB + 256 B, present on
  * every device that loads this library until the process exits. The first
  * call on a device looks up that array's address (cudaGetSymbolAddress, with
  * the device current); make that first call before any stream capture. All

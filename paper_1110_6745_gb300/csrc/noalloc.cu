@@ -29,6 +29,8 @@ constexpr int64_t kNoallocMaxL = 131072;
 constexpr size_t kNoallocHcolBytes = (size_t)kNoallocMaxL * sizeof(int64_t);      // 1 MiB
 constexpr size_t kNoallocPartialBytes = (size_t)kMaxReduceBlocks * 8 * sizeof(uint64_t);
 constexpr size_t kNoallocBytes = kNoallocHcolBytes + kNoallocPartialBytes + sizeof(Ctrl);
+// 1 MiB of column heights + 128 KiB of partial sums + the 256-byte result block
+static_assert(kNoallocBytes == (1u << 20) + (128u << 10) + 256u, "documented scratch size");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 
@@ -74,6 +76,11 @@ extern "C" okz_status okz_width2_noalloc(const uint32_t *planes, int64_t L, int6
                                          double *W2) {
   if (!planes || L < 32 || (L % 32) != 0) {
     set_error("okz_width2_noalloc: planes must be non-null and L a multiple of 32");
+    return OKZ_EINVAL;
+  }
+  if (((uintptr_t)planes & 15u) != 0) {
+    // the row kernels read the planes with 16-byte vector loads
+    set_error("okz_width2_noalloc: planes must be 16-byte aligned");
     return OKZ_EINVAL;
   }
   if (L > kNoallocMaxL) {

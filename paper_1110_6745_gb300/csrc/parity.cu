@@ -404,7 +404,7 @@ parity_stream_kernel(const uint32_t *__restrict__ src, uint32_t *__restrict__ ds
         // give copies already issued a bounded chance to land before exiting
         int issued = (i >= 2 ? i - 2 : 0) + stages;
         if (issued > nin) issued = nin;
-        for (int k = i + 1; k < issued; ++k)
+        for (int k = i; k < issued; ++k)
           (void)tma::mbar_wait(&full[k % stages], (uint32_t)((k / stages) & 1));
       }
       return;

@@ -30,61 +30,11 @@
 #include <cuda_runtime.h>
 
 #include "okz_internal.h"
+#include "okz_tma.cuh"
 
 namespace okz {
 
 namespace {
-
-__device__ __forceinline__ uint32_t smem_addr(const void *p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
-               : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
-               "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_addr(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Bounded wait: true when the phase completed, false after kWaitLimitNs.
-__device__ __noinline__ bool mbar_wait_slow(uint64_t *bar, uint32_t parity) {
-  const uint64_t start = globaltimer_ns();
-  while (true) {
-    for (int i = 0; i < 64; ++i)
-      if (mbar_try_wait(bar, parity)) return true;
-    if (globaltimer_ns() - start > kWaitLimitNs) return false;
-  }
-}
-
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
-  if (mbar_try_wait(bar, parity)) return true;
-  return mbar_wait_slow(bar, parity);
-}
-
-__device__ __forceinline__ void tma_load_1d(void *dst_smem, const void *src_gmem,
-                                            uint32_t bytes, uint64_t *bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-          "r"(smem_addr(dst_smem)),
-      "l"(src_gmem), "r"(bytes), "r"(smem_addr(bar))
-      : "memory");
-}
 
 // Acceptance modes.
 //  kModeHalf: k = 1, P = 1, Q = 0 -- a minimum moves iff its level-0 bit is 0
@@ -193,16 +143,16 @@ sweep_stream_kernel(const uint32_t *__restrict__ src, uint32_t *__restrict__ dst
   int p_slot = 0;
   auto issue = [&]() {
     unsigned char *d = ring + (size_t)p_slot * 2 * rowbytes;
-    mbar_expect_tx(&full[p_slot], 2 * rowbytes);
-    tma_load_1d(d, src + (size_t)p_row * W, rowbytes, &full[p_slot]);
-    tma_load_1d(d + rowbytes, src + plane_words + (size_t)p_row * W, rowbytes, &full[p_slot]);
+    tma::mbar_expect_tx(&full[p_slot], 2 * rowbytes);
+    tma::load_1d(d, src + (size_t)p_row * W, rowbytes, &full[p_slot]);
+    tma::load_1d(d + rowbytes, src + plane_words + (size_t)p_row * W, rowbytes, &full[p_slot]);
     if (++p_row == L) p_row = 0;
     if (++p_slot == stages) p_slot = 0;
   };
 
   if (tid == 0) {
-    for (int s = 0; s < stages; ++s) mbar_init(&full[s], 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    for (int s = 0; s < stages; ++s) tma::mbar_init(&full[s], 1);
+    tma::mbar_init_fence();
   }
   __syncthreads();
   if (tid == 0)
@@ -237,7 +187,7 @@ sweep_stream_kernel(const uint32_t *__restrict__ src, uint32_t *__restrict__ dst
   const int r_origin = yb - 2 * F;  // unwrapped row of stream position 0
 
   for (int i = 0; i < nin; ++i) {
-    const bool ok = mbar_wait_bounded(&full[slot], phase);
+    const bool ok = tma::mbar_wait(&full[slot], phase);
     const unsigned char *d = ring + (size_t)slot * 2 * rowbytes;
     uint32_t Xr[WPT], Yr[WPT];
 #pragma unroll
@@ -317,14 +267,16 @@ sweep_stream_kernel(const uint32_t *__restrict__ src, uint32_t *__restrict__ dst
       if (tid == 0) {
         atomicOr(&ctrl->err, kErrWaitTimeout);
         // give copies already issued a bounded chance to land before exiting
+        // (positions i .. i + stages - 1; the wait on position i itself
+        // failed, so it gets one more bounded wait as well)
         int sl = slot;
         uint32_t ph = phase;
-        for (int k = i + 1; k < nin && k < i + stages; ++k) {
+        for (int k = i; k < nin && k < i + stages; ++k) {
+          (void)tma::mbar_wait(&full[sl], ph);
           if (++sl == stages) {
             sl = 0;
             ph ^= 1u;
           }
-          (void)mbar_wait_bounded(&full[sl], ph);
         }
       }
       return;
@@ -334,7 +286,7 @@ sweep_stream_kernel(const uint32_t *__restrict__ src, uint32_t *__restrict__ dst
 
     // the slot of this row is free: refill it with row i + stages
     if (tid == 0 && i + stages < nin) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      tma::fence_proxy_async();
       issue();
     }
 

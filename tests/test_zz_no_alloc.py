@@ -63,3 +63,8 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(okz):
     assert "scratch" in okz.okz_last_error()
     with pytest.raises(okz.OkzError):
         okz.okz_width2_noalloc(dummy.data_ptr(), 100, 0, None)
+    # an offset view of a tensor: not 16-byte aligned, refused before any launch
+    with pytest.raises(okz.OkzError) as e:
+        okz.okz_width2_noalloc(dummy.data_ptr() + 4, 32, 0, None)
+    assert e.value.status == okz.OKZ_EINVAL
+    assert "aligned" in okz.okz_last_error()
