@@ -362,27 +362,46 @@ def _invariants_on_device(planes_dev, L):
     assert bool((colsum == L // 2).all()), "column of sigma_y does not sum to 0"
 
 
+def _check_windows(orc, planes, L, p, q, seed, n, windows):
+    """Each window's core (farther than 2n + 1 from its edges) equals the
+    oracle's light-cone simulation of the same window, site by site."""
+    m = 2 * n + 2
+    for (x0, y0, cw, ch) in windows:
+        w, h = cw + 2 * m, ch + 2 * m
+        x0, y0 = (x0 - m) % L, (y0 - m) % L
+        WX, WY = orc.window_flat_sweeps(L, x0, y0, w, h, p, q, seed, n)
+        GX, GY = _unpack_window(planes, L, x0, y0, w, h)
+        assert np.array_equal(GX[m:h - m, m:w - m], WX[m:h - m, m:w - m]), (x0, y0)
+        assert np.array_equal(GY[m:h - m, m:w - m], WY[m:h - m, m:w - m]), (x0, y0)
+
+
+# Window cores (x, y, width, height) at L = 2^17 for the benchmark's launch
+# shape (152 bands of ~862 rows, 256 threads of 16 words per row, 2 sweeps
+# per launch): two band boundaries (y = 862, 1724) and a warp boundary
+# (x = 16384); the periodic corner (both wraps); the last band boundary
+# (y = 130209) with a thread boundary (x = 70144).
+WINDOWS_L131072 = [(16300, 780, 200, 1020), ((1 << 17) - 100, (1 << 17) - 100, 200, 200),
+                   (70100, 130100, 200, 200)]
+
+
 def test_full_size_L131072(okz, orc):
-    """The headline lattice in the benchmark's launch configuration: windows
-    checked site by site against the oracle's light-cone simulation, global
-    invariants on the device, sampled heights against Eq. (3) evaluated by
-    the oracle, and the exact sums against an independent chunked reduction."""
+    """The headline lattice in the benchmark's launch configuration after 512
+    sweeps: windows checked site by site against the oracle's light-cone
+    simulation across CTA band, warp and thread boundaries and both periodic
+    wraps, global invariants on the device, sampled heights against Eq. (3)
+    evaluated by the oracle, and the exact sums against an independent
+    chunked reduction."""
     import torch
-    L, n, seed = 1 << 17, 8, 11
+    L, n, seed = 1 << 17, 512, 11
     with okz.Simulation(L, 1.0, 0.0, seed=seed) as sim:
-        assert sim.info().kernel == okz.OKZ_KERNEL_PARITY_STREAM
+        info = sim.info()
+        assert info.kernel == okz.OKZ_KERNEL_PARITY_STREAM
+        assert (info.words_per_thread, info.sweeps_per_pass) == (16, 2)
         sim.sweep(n)
         planes = torch.empty((2, L, L // 32), dtype=torch.int32, device="cuda")
         _, H0, t = sim.state(out=planes)
         assert t == n
-        m = 2 * n + 2
-        for (x0, y0) in [(1000, 2000), (L - 40, L - 40), (70000, 862 - 60), (0, 0),
-                         (L - 150, 5000)]:
-            w = h = 160
-            WX, WY = orc.window_flat_sweeps(L, x0, y0, w, h, 1.0, 0.0, seed, n)
-            GX, GY = _unpack_window(planes, L, x0, y0, w, h)
-            assert np.array_equal(GX[m:h - m, m:w - m], WX[m:h - m, m:w - m]), (x0, y0)
-            assert np.array_equal(GY[m:h - m, m:w - m], WY[m:h - m, m:w - m]), (x0, y0)
+        _check_windows(orc, planes, L, 1.0, 0.0, seed, n, WINDOWS_L131072)
         _invariants_on_device(planes, L)
         # sampled heights against the oracle's path sum on the host copy
         host = planes.cpu().numpy().view(np.uint32)
@@ -403,6 +422,39 @@ def test_full_size_L131072(okz, orc):
         N = L * L
         assert W2 == float(N * s2 - s1 * s1) / (float(N) * float(N)) or \
             W2 == pytest.approx((N * s2 - s1 * s1) / N / N, rel=1e-15)
+
+
+def test_full_size_L131072_minima_and_maxima(okz, orc):
+    """p = q = 1 (k = 1, both branches of the rule, the two-threshold kernel)
+    at L = 2^17 in the benchmark's launch shape: 512 sweeps, windows across
+    band, warp and thread boundaries and the periodic corner against the
+    oracle, and the device invariants."""
+    import torch
+    L, n, seed = 1 << 17, 512, 13
+    with okz.Simulation(L, 1.0, 1.0, seed=seed) as sim:
+        info = sim.info()
+        assert (info.words_per_thread, info.sweeps_per_pass) == (16, 2)
+        sim.sweep(n)
+        planes = torch.empty((2, L, L // 32), dtype=torch.int32, device="cuda")
+        sim.state(out=planes)
+        _check_windows(orc, planes, L, 1.0, 1.0, seed, n, WINDOWS_L131072[:2])
+        _invariants_on_device(planes, L)
+
+
+def test_wpt16_two_sweep_kernel_against_oracle_L32768(okz, orc):
+    """The 16-word, two-sweeps-per-launch kernel at L = 2^15 (152 bands of
+    ~215 rows, two warps per row) against the full-lattice oracle after 64
+    sweeps: every bond, H0 and the exact sums."""
+    L, n, seed = 32768, 64, 19
+    ref = orc.Sim(L, 1.0, 0.0, seed)
+    ref.sweep(n)
+    with okz.Simulation(L, 1.0, 0.0, seed=seed) as sim:
+        info = sim.info()
+        assert (info.words_per_thread, info.sweeps_per_pass) == (16, 2)
+        sim.sweep(n)
+        _compare(sim, ref)
+        S1, S2, W2 = sim.width2()
+        assert (S1, S2) == ref.sums() and W2 == ref.width2()
 
 
 def _golden_rows(path):
