@@ -112,6 +112,9 @@ typedef struct okz_info {
     size_t device_bytes;  /* device memory held by the simulation              */
     int32_t words_per_thread;  /* stream kernels: words per thread (else 0)    */
     int32_t sweeps_per_pass;   /* sweeps per launch                             */
+    int32_t graph_chunk;       /* in-place kernels: sweeps per replay of the
+                                  simulation's CUDA graph (0 = not built)       */
+    uint64_t graph_replays;    /* replays of that graph so far                  */
 } okz_info;
 
 typedef struct okz_sim okz_sim;
@@ -153,8 +156,14 @@ okz_status okz_create_ex(const okz_params *prm, void *dev_buf, size_t bytes,
                          void *stream, okz_sim **out);
 
 /* Enqueues n >= 0 sweeps (Sec. II: one sweep = one MCS) on the simulation's
- * stream and returns without waiting. Errors: EINVAL (n < 0), EOVERFLOW
- * (t + n > 2^32 - 1; nothing is enqueued), ECUDA (launch failure). */
+ * stream and returns without waiting. The stream kernels take one launch per
+ * sweeps_per_pass sweeps. The in-place kernels (PLAIN, PARITY_PLAIN: two
+ * launches per sweep) run whole chunks of 32 sweeps by replaying one CUDA
+ * graph, captured on the first call with n >= 32, whose launches read the
+ * chunk's first sweep index from the simulation's device control block; the
+ * rest of n goes as direct launches. Results do not depend on the split.
+ * Errors: EINVAL (n < 0), EOVERFLOW (t + n > 2^32 - 1; nothing is
+ * enqueued), ECUDA (launch failure). */
 okz_status okz_sweep(okz_sim *sim, int64_t n);
 
 /* Enqueues n sweeps of the domain-decomposed random-sequential dynamics, the
@@ -273,6 +282,20 @@ const char *okz_last_error(void);
  * = the legacy default stream); synchronizing; uses 4 bytes of
  * stream-ordered device memory. Errors: ENOMEM, ECUDA. */
 okz_status okz_selftest_wait_timeout(void *stream);
+
+/* okz_alu_peak -- the paper has no counterpart to this entry point. A
+ * diagnostic that measures the INT32 ALU-pipe throughput of the current
+ * device, the denominator of the sweep kernels' roofline (their update logic
+ * and most of the Philox work are three-input logic ops and funnel shifts,
+ * which issue to that pipe). Launches 8 blocks of 256 threads per SM, each
+ * thread running 8 independent chains of `iters` lop3.b32 ops (no memory
+ * traffic in the loop); one warm-up launch, then the best of three timed
+ * launches (CUDA events on `stream`, a cudaStream_t, NULL = the legacy
+ * default stream). Writes the rate in thread-ops per second to *ops_per_s and
+ * the best launch time to *best_ms (may be NULL). Synchronizing; allocates
+ * nothing. iters of 20000 give launches of about 2.5 ms on GB300. Errors:
+ * EINVAL (iters < 1 or ops_per_s NULL), ECUDA. */
+okz_status okz_alu_peak(void *stream, int32_t iters, double *ops_per_s, double *best_ms);
 
 /* okz_width2_noalloc -- the paper has no counterpart to this entry point; it
  * serves callers that cannot allocate device memory when they measure, e.g.

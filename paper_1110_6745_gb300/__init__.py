@@ -48,7 +48,8 @@ class okz_info(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int64), ("t", ctypes.c_uint64), ("H0", ctypes.c_int64),
                 ("k", ctypes.c_int32), ("kernel", ctypes.c_int32), ("P", ctypes.c_uint64),
                 ("Q", ctypes.c_uint64), ("device_bytes", ctypes.c_size_t),
-                ("words_per_thread", ctypes.c_int32), ("sweeps_per_pass", ctypes.c_int32)]
+                ("words_per_thread", ctypes.c_int32), ("sweeps_per_pass", ctypes.c_int32),
+                ("graph_chunk", ctypes.c_int32), ("graph_replays", ctypes.c_uint64)]
 
 
 # C signatures: name -> (restype, argtypes)
@@ -71,6 +72,8 @@ _SIGS = {
     "okz_profiles": (_c.c_int, [_vp, _vp, _vp]),
     "okz_moments_enqueue": (_c.c_int, [_vp]),
     "okz_selftest_wait_timeout": (_c.c_int, [_vp]),
+    "okz_alu_peak": (_c.c_int, [_vp, _c.c_int32, _c.POINTER(_c.c_double),
+                                _c.POINTER(_c.c_double)]),
     "okz_moments_fetch": (_c.c_int, [_vp, _c.POINTER(okz_i128), _c.POINTER(_c.c_double),
                                _c.POINTER(_c.c_double), _c.POINTER(_c.c_double)]),
     "okz_psd": (_c.c_int, [_vp, _vp]),
@@ -193,6 +196,14 @@ def okz_selftest_wait_timeout(stream=None):
     """Runs the bounded-wait self-test; raises OkzError(OKZ_ETIMEOUT) when the
     wait gave up as intended, returns if it (wrongly) completed."""
     _check(lib().okz_selftest_wait_timeout(stream), "okz_selftest_wait_timeout")
+
+
+def okz_alu_peak(stream=None, iters=20000):
+    """Measured INT32 ALU-pipe rate of the current device -> (ops/s, best ms)."""
+    ops, ms = ctypes.c_double(), ctypes.c_double()
+    _check(lib().okz_alu_peak(stream, int(iters), ctypes.byref(ops), ctypes.byref(ms)),
+           "okz_alu_peak")
+    return ops.value, ms.value
 
 
 def okz_moments_enqueue(h):

@@ -14,7 +14,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libokz.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 SOURCES = ["capi.cu", "sweep_plain.cu", "sweep_stream.cu", "measure.cu", "parity.cu",
-           "noalloc.cu", "batch.cu", "batch_capi.cu", "psd.cu", "ddrs.cu", "convert.cu", "selftest.cu"]
+           "noalloc.cu", "batch.cu", "batch_capi.cu", "psd.cu", "ddrs.cu", "convert.cu", "selftest.cu", "peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-Wall",
               "-I", INCLUDE, "-I", CSRC] + ARCH

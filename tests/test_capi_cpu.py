@@ -82,3 +82,10 @@ def test_null_handles_are_rejected(okz):
     with pytest.raises(okz.OkzError):
         okz.okz_sweep(None, -1)
     okz.okz_destroy(None)  # accepted
+
+
+def test_alu_peak_rejects_bad_arguments(okz):
+    """okz_alu_peak checks its arguments before touching the device."""
+    with pytest.raises(okz.OkzError) as e:
+        okz.okz_alu_peak(None, 0)
+    assert e.value.status == okz.OKZ_EINVAL
