@@ -32,6 +32,12 @@ struct okz_sim {
   unsigned long long *partials;
   okz::Ctrl *ctrl;
   uint64_t t;
+  // in-place (plain) kernels: a CUDA graph of kGraphChunk sweeps that reads
+  // its first sweep from ctrl->t_base and advances it; 0 = not built yet,
+  // 1 = built, -1 = capture failed (direct launches only)
+  cudaGraphExec_t sweep_graph;
+  int graph_state;
+  uint64_t graph_replays;
 };
 
 namespace okz {
@@ -335,6 +341,65 @@ okz_status okz_create(int64_t L, double p, double q, uint64_t seed, okz_sim **ou
   return okz_create_ex(&prm, nullptr, 0, nullptr, out);
 }
 
+namespace {
+
+// Sweeps replayed per launch of a simulation's sweep graph.
+constexpr int64_t kGraphChunk = 32;
+
+// The two half-sweeps of sweep t (t_base set: of sweep t + *t_base) of an
+// in-place (plain) kernel.
+cudaError_t enqueue_inplace_sweep(okz_sim *sim, uint32_t t, cudaStream_t st,
+                                  const unsigned int *t_base) {
+  const int64_t L = sim->prm.L;
+  cudaError_t e;
+  if (sim->parity) {
+    e = launch_parity_halfsweep(sim->planes[sim->cur], L, 0, t, sim->prm.seed, sim->acc,
+                                sim->ctrl, st, t_base);
+    if (e == cudaSuccess)
+      e = launch_parity_halfsweep(sim->planes[sim->cur], L, 1, t, sim->prm.seed, sim->acc,
+                                  sim->ctrl, st, t_base);
+  } else {
+    e = launch_halfsweep_plain(sim->planes[sim->cur], L, 0, t, sim->prm.seed, sim->acc,
+                               sim->ctrl, st, t_base);
+    if (e == cudaSuccess)
+      e = launch_halfsweep_plain(sim->planes[sim->cur], L, 1, t, sim->prm.seed, sim->acc,
+                                 sim->ctrl, st, t_base);
+  }
+  return e;
+}
+
+// Captures kGraphChunk in-place sweeps (2 launches each, sweep indices read
+// from ctrl->t_base) plus the advance of ctrl->t_base into one CUDA graph.
+// The graph's pointers are the simulation's own (in-place kernels never swap
+// buffers), so it is built once and replayed for every later chunk.
+void build_sweep_graph(okz_sim *sim) {
+  cudaStream_t cs;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    sim->graph_state = -1;
+    return;
+  }
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  for (int64_t k = 0; k < kGraphChunk && e == cudaSuccess; ++k)
+    e = enqueue_inplace_sweep(sim, (uint32_t)k, cs, &sim->ctrl->t_base);
+  if (e == cudaSuccess) e = launch_advance_sweep_counter(sim->ctrl, (uint32_t)kGraphChunk, cs);
+  const cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&sim->sweep_graph, g, 0);
+  if (g) cudaGraphDestroy(g);
+  cudaStreamDestroy(cs);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    sim->sweep_graph = nullptr;
+    sim->graph_state = -1;
+    return;
+  }
+  sim->graph_state = 1;
+}
+
+}  // namespace
+
 okz_status okz_sweep(okz_sim *sim, int64_t n) {
   if (!sim || n < 0) {
     set_error("null simulation or negative sweep count");
@@ -346,6 +411,20 @@ okz_status okz_sweep(okz_sim *sim, int64_t n) {
   }
   const int64_t L = sim->prm.L;
   int64_t done = 0;
+  const bool inplace = sim->kernel == OKZ_KERNEL_PLAIN || sim->kernel == OKZ_KERNEL_PARITY_PLAIN;
+  if (inplace && n >= kGraphChunk) {  // whole chunks by graph replay
+    if (sim->graph_state == 0) build_sweep_graph(sim);
+    if (sim->graph_state == 1) {
+      cudaError_t e = launch_set_sweep_counter(sim->ctrl, (uint32_t)sim->t, sim->stream);
+      const int64_t chunks = n / kGraphChunk;
+      for (int64_t c = 0; c < chunks && e == cudaSuccess; ++c)
+        e = cudaGraphLaunch(sim->sweep_graph, sim->stream);
+      if (e != cudaSuccess) return cuda_fail(e, "sweep graph launch");
+      sim->graph_replays += (uint64_t)chunks;
+      done = chunks * kGraphChunk;
+      sim->t += (uint64_t)done;
+    }
+  }
   while (done < n) {
     const uint32_t t = (uint32_t)sim->t;
     cudaError_t e;
@@ -361,18 +440,8 @@ okz_status okz_sweep(okz_sim *sim, int64_t n) {
                                 sim->prm.seed, sim->acc, sim->wpt, (int)step, sim->ctrl,
                                 sim->stream);
       if (e == cudaSuccess) sim->cur = 1 - sim->cur;
-    } else if (sim->parity) {
-      e = launch_parity_halfsweep(sim->planes[sim->cur], L, 0, t, sim->prm.seed, sim->acc,
-                                  sim->ctrl, sim->stream);
-      if (e == cudaSuccess)
-        e = launch_parity_halfsweep(sim->planes[sim->cur], L, 1, t, sim->prm.seed, sim->acc,
-                                    sim->ctrl, sim->stream);
     } else {
-      e = launch_halfsweep_plain(sim->planes[sim->cur], L, 0, t, sim->prm.seed, sim->acc,
-                                 sim->ctrl, sim->stream);
-      if (e == cudaSuccess)
-        e = launch_halfsweep_plain(sim->planes[sim->cur], L, 1, t, sim->prm.seed, sim->acc,
-                                   sim->ctrl, sim->stream);
+      e = enqueue_inplace_sweep(sim, t, sim->stream, nullptr);
     }
     if (e != cudaSuccess) return cuda_fail(e, "sweep launch");
     sim->t += (uint64_t)step;
@@ -714,6 +783,8 @@ okz_status okz_get_info(okz_sim *sim, okz_info *info) {
   okz_status st = okz_state(sim, nullptr, 0, &H0, nullptr);
   if (st != OKZ_OK) return st;
   info->L = sim->prm.L;
+  info->graph_chunk = sim->graph_state == 1 ? (int32_t)kGraphChunk : 0;
+  info->graph_replays = sim->graph_replays;
   info->t = sim->t;
   info->H0 = H0;
   info->k = sim->acc.k;
@@ -729,6 +800,7 @@ okz_status okz_get_info(okz_sim *sim, okz_info *info) {
 okz_status okz_destroy(okz_sim *sim) {
   if (!sim) return OKZ_OK;
   cudaError_t e = cudaStreamSynchronize(sim->stream);
+  if (sim->sweep_graph) cudaGraphExecDestroy(sim->sweep_graph);
   if (sim->own_mem) cudaFree(sim->base);
   if (sim->own_stream) cudaStreamDestroy(sim->stream);
   delete sim;

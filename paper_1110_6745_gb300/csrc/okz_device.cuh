@@ -165,7 +165,7 @@ constexpr uint32_t kErrHeightRange = 2u;
 struct Ctrl {
   long long H0;           // h(0,0)
   unsigned int err;       // kErr* bits
-  unsigned int pad0;
+  unsigned int t_base;     // sweep counter read by graph-replayed half-sweeps
   unsigned long long sum[8];  // exact sums as (lo, hi) pairs: S1, S2, S3, S4
   unsigned long long pad1[22];
 };

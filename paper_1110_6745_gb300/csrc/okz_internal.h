@@ -27,9 +27,13 @@ okz_status cuda_fail(cudaError_t e, const char *what);
 
 // ---- launchers (each returns cudaGetLastError() of its launches) ----------
 cudaError_t launch_init_flat(uint32_t *planes, int64_t L, cudaStream_t st);
+// t_base (device, may be null): added to t, for graph-replayed chunks of sweeps.
 cudaError_t launch_halfsweep_plain(uint32_t *planes, int64_t L, int s, uint32_t t,
                                    uint64_t seed, const Accept &acc, Ctrl *ctrl,
-                                   cudaStream_t st);
+                                   cudaStream_t st, const unsigned int *t_base = nullptr);
+// ctrl->t_base = t, and ctrl->t_base += n (one-thread kernels, stream-ordered).
+cudaError_t launch_set_sweep_counter(Ctrl *ctrl, uint32_t t, cudaStream_t st);
+cudaError_t launch_advance_sweep_counter(Ctrl *ctrl, uint32_t n, cudaStream_t st);
 bool stream_kernel_supports(int64_t L);
 // Words per thread the stream kernel can use for L (4 or 8; 0 = not valid).
 bool stream_wpt_valid(int64_t L, int wpt);
@@ -52,7 +56,8 @@ cudaError_t launch_heights(const uint32_t *planes, int64_t L, bool parity, int64
 // blocked random-sequential sweep (ddrs.cu), and the conversions to and from
 // the slope planes of the C-ABI state format (convert.cu).
 cudaError_t launch_parity_halfsweep(uint32_t *B, int64_t L, int s, uint32_t t, uint64_t seed,
-                                    const Accept &acc, Ctrl *ctrl, cudaStream_t st);
+                                    const Accept &acc, Ctrl *ctrl, cudaStream_t st,
+                                    const unsigned int *t_base = nullptr);
 // The parity stream kernel also takes 16 words per thread: L % 16384 == 0.
 bool parity_wpt_valid(int64_t L, int wpt);
 cudaError_t launch_parity_stream(const uint32_t *src, uint32_t *dst, int64_t L, uint32_t t,

@@ -48,9 +48,13 @@ __device__ __forceinline__ void parity_extrema(uint32_t c, uint32_t l, uint32_t 
 // on a site of the other sublattice, which nobody writes in this half-sweep;
 // whole-word stores therefore never change a bit another thread uses.
 // ---------------------------------------------------------------------------
+// (t_base: as in the slope-plane half-sweep, the first sweep of a graph
+// chunk read from device memory; t is then the offset within the chunk)
 __global__ void __launch_bounds__(256)
-parity_halfsweep_kernel(uint32_t *__restrict__ B, int64_t L, int s, uint32_t t,
-                        const RoundKeys rk, Accept acc, Ctrl *__restrict__ ctrl) {
+parity_halfsweep_kernel(uint32_t *__restrict__ B, int64_t L, int s, uint32_t t_off,
+                        const unsigned int *__restrict__ t_base, const RoundKeys rk, Accept acc,
+                        Ctrl *__restrict__ ctrl) {
+  const uint32_t t = t_off + (t_base ? *t_base : 0u);
   const int64_t W = L >> 5;
   const int64_t groups = L * W >> 2;
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -102,10 +106,11 @@ parity_halfsweep_kernel(uint32_t *__restrict__ B, int64_t L, int s, uint32_t t,
 }
 
 cudaError_t launch_parity_halfsweep(uint32_t *B, int64_t L, int s, uint32_t t, uint64_t seed,
-                                    const Accept &acc, Ctrl *ctrl, cudaStream_t st) {
+                                    const Accept &acc, Ctrl *ctrl, cudaStream_t st,
+                                    const unsigned int *t_base) {
   const int64_t groups = L * (L >> 5) / 4;
   parity_halfsweep_kernel<<<(unsigned)((groups + 255) / 256), 256, 0, st>>>(
-      B, L, s, t, round_keys(seed), acc, ctrl);
+      B, L, s, t, t_base, round_keys(seed), acc, ctrl);
   return cudaGetLastError();
 }
 

@@ -34,11 +34,15 @@ cudaError_t launch_init_flat(uint32_t *planes, int64_t L, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-// Half-sweep s of sweep t. acc.k levels of random bits at most; the level
+// Half-sweep s of sweep t (plus *t_base when t_base is set: the launches of a
+// CUDA graph replayed for consecutive chunks of sweeps read the chunk's first
+// sweep from device memory). acc.k levels of random bits at most; the level
 // loop stops as soon as no extremum of the group is still undecided.
 __global__ void __launch_bounds__(256)
-halfsweep_plain_kernel(uint32_t *__restrict__ planes, int64_t L, int s, uint32_t t,
-                       uint64_t seed, Accept acc, Ctrl *__restrict__ ctrl) {
+halfsweep_plain_kernel(uint32_t *__restrict__ planes, int64_t L, int s, uint32_t t_off,
+                       const unsigned int *__restrict__ t_base, uint64_t seed, Accept acc,
+                       Ctrl *__restrict__ ctrl) {
+  const uint32_t t = t_off + (t_base ? *t_base : 0u);
   const int64_t W = L >> 5;
   const int64_t words = L * W;
   const int64_t groups = words >> 2;
@@ -106,11 +110,30 @@ halfsweep_plain_kernel(uint32_t *__restrict__ planes, int64_t L, int s, uint32_t
 
 cudaError_t launch_halfsweep_plain(uint32_t *planes, int64_t L, int s, uint32_t t,
                                    uint64_t seed, const Accept &acc, Ctrl *ctrl,
-                                   cudaStream_t st) {
+                                   cudaStream_t st, const unsigned int *t_base) {
   const int64_t groups = L * (L >> 5) / 4;
   const int64_t blocks = (groups + 255) / 256;
-  halfsweep_plain_kernel<<<(unsigned)blocks, 256, 0, st>>>(planes, L, s, t, seed, acc,
+  halfsweep_plain_kernel<<<(unsigned)blocks, 256, 0, st>>>(planes, L, s, t, t_base, seed, acc,
                                                            ctrl);
+  return cudaGetLastError();
+}
+
+namespace {
+__global__ void sweep_counter_kernel(Ctrl *__restrict__ ctrl, uint32_t v, int add) {
+  if (add)
+    ctrl->t_base += v;
+  else
+    ctrl->t_base = v;
+}
+}  // namespace
+
+cudaError_t launch_set_sweep_counter(Ctrl *ctrl, uint32_t t, cudaStream_t st) {
+  sweep_counter_kernel<<<1, 1, 0, st>>>(ctrl, t, 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_advance_sweep_counter(Ctrl *ctrl, uint32_t n, cudaStream_t st) {
+  sweep_counter_kernel<<<1, 1, 0, st>>>(ctrl, n, 1);
   return cudaGetLastError();
 }
 

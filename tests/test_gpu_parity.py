@@ -221,6 +221,26 @@ def test_growth_series_L256(okz, orc, kernel):
         _compare(sim, ref)
 
 
+@pytest.mark.parametrize("kernel", PLAIN_KINDS)
+@pytest.mark.parametrize("L,p,q", [(64, 0.75, 0.25), (256, 1.0, 0.0), (480, 0.95, 0.05)])
+def test_inplace_sweeps_by_graph_replay(okz, orc, L, p, q, kernel):
+    """n >= 32 sweeps of the in-place kernels go as replays of one CUDA graph
+    of 32 sweeps (sweep index from device memory) plus direct launches for
+    the rest: 100 = 3 x 32 + 4, then 37 = 32 + 5; lattice, H0 and sums equal
+    the oracle's after each call."""
+    seed = 300 + L
+    ref = orc.Sim(L, p, q, seed)
+    with okz.Simulation(L, p, q, seed=seed, kernel=kernel) as sim:
+        for n, replays in ((100, 3), (37, 4)):
+            ref.sweep(n)
+            sim.sweep(n)
+            _compare(sim, ref)
+            info = sim.info()
+            assert (info.graph_chunk, info.graph_replays) == (32, replays)
+            S1, S2, W2 = sim.width2()
+            assert (S1, S2) == ref.sums() and W2 == ref.width2()
+
+
 def test_growth_series_helper_matches_oracle(okz, orc):
     """analysis.growth_series (the product's sampling loop) at L = 256,
     1000 sweeps, 20 samples: every record equals the oracle's."""
