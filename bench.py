@@ -154,6 +154,31 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def measure_alu_peak(okz, local, stream=None):
+    """The INT32 ALU-pipe rate of this GPU measured by the library's
+    okz_alu_peak (independent lop3.b32 chains), with the SM clock sampled
+    while it runs, and the derived figure (152 SMs x 64 lanes x that clock)
+    beside it as a cross-check."""
+    okz.okz_alu_peak(stream, 2000)  # warm-up (module load, clocks up)
+    clk = ClockSampler(local)
+    clk.start()
+    best = 0.0
+    for _ in range(20):  # about 1 s, so that the clock sampler sees the run
+        ops, _ = okz.okz_alu_peak(stream, 20000)
+        best = max(best, ops)
+    c = clk.stop()
+    mhz = (c or {}).get("sm_mhz") or 2070.0
+    return {"value": best / 1e12, "unit": "Tops/s", "sm_mhz": mhz,
+            "ops_per_sm_per_clk": best / N_SMS / (mhz * 1e6),
+            "derived": N_SMS * ALU_LANES_PER_SM * mhz * 1e6 / 1e12,
+            "clocks": c, "kernel": "okz_alu_peak (8 independent lop3.b32 chains per thread)"}
+
+
+def _alu_peak_at(peak, sm_mhz):
+    """The measured ALU-pipe rate scaled to the SM clock of a timed region."""
+    return peak["value"] * sm_mhz / peak["sm_mhz"]
+
+
 def _dist_init(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -257,6 +282,7 @@ def run_gpu(args, world, rank, local):
         sim = okz.Simulation(L, 1.0, 0.0, seed=SEED + rank, torch_buffer=True,
                              kernel=KERNELS[args.kernel], words_per_thread=args.wpt,
                              sweeps_per_pass=args.fuse)
+    peak_meas = measure_alu_peak(okz, local, stream.cuda_stream)
     kind = sim.info().kernel
     assert kind in (okz.OKZ_KERNEL_STREAM, okz.OKZ_KERNEL_PARITY_STREAM)
     repr_name = "parity" if kind == okz.OKZ_KERNEL_PARITY_STREAM else "slope"
@@ -309,49 +335,38 @@ def run_gpu(args, world, rank, local):
     peak, peak_kind = _peaks()
     traffic = _traffic(repr_name, N) if fuse == 2 else None  # measured at 2 sweeps/launch
     # ALU roof: algorithmic ALU-pipe ops per launch / launch time, against
-    # 152 SMs x 64 lanes x the SM clock sampled during the timed region
+    # the ALU-pipe rate measured on this GPU (okz_alu_peak) at the SM clock
+    # sampled during the timed region
     sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
-    alu_peak = N_SMS * ALU_LANES_PER_SM * sm_mhz * 1e6 / 1e12
+    alu_peak = _alu_peak_at(peak_meas, sm_mhz)
     alu_ops = ALU_OPS_PER_SITE_SWEEP[repr_name] * N * fuse
     alu_achieved = alu_ops / per_launch_s / 1e12
 
-    # end to end through the C-ABI with host buffers: every step's input (the
-    # whole lattice state, 4 GiB) comes from pinned host memory and its exact
-    # sums go back to the host. Step k+1's input is copied on a copy stream
-    # while step k sweeps (two device staging buffers); all copies lie inside
-    # the timed region.
+    # end to end through the C-ABI with host buffers: every step's input, the
+    # whole lattice state (both slope planes, 4 GiB), goes in from pinned host
+    # memory through okz_restore (the library's host-to-device copy and its
+    # conversion to the parity plane), then 256 sweeps, then the exact sums
+    # come back (okz_width2). All copies lie inside the timed region; one
+    # untimed step first (the first copy from freshly pinned memory pays a
+    # one-time mapping cost).
     e2e_steps = min(args.steps, 8)
     host_planes = torch.empty(2 * L * L // 32, dtype=torch.int32, pin_memory=True)
     host_planes.copy_(start_planes.cpu())
-    staging = [torch.empty_like(start_planes) for _ in range(2)]
-    copy_stream = torch.cuda.Stream(device=dev)
-    ready = [torch.cuda.Event() for _ in range(2)]
+    del start_planes
 
-    def prefetch(k):
-        with torch.cuda.stream(copy_stream):
-            staging[k % 2].copy_(host_planes, non_blocking=True)
-            ready[k % 2].record(copy_stream)
-
-    def e2e_step(k, last):
-        stream.wait_event(ready[k % 2])
-        sim.restore(staging[k % 2], 0, 0)  # device-to-device + conversion, synchronous
-        if not last:
-            prefetch(k + 1)
+    def e2e_step():
+        sim.restore(host_planes, 0, 0)  # H2D inside the library, synchronous
         sim.sweep(SWEEPS_PER_STEP)
         return sim.width2()
 
-    # untimed warm-up of the end-to-end leg: the first DMA from a freshly
-    # pinned buffer pays a one-time mapping cost
-    prefetch(0)
-    e2e_step(0, True)
+    e2e_step()
     torch.cuda.synchronize(dev)
     _barrier(world)
     e2e_clocks = ClockSampler(local)
     e2e_clocks.start()
     t0 = time.perf_counter()
-    prefetch(0)
-    for k in range(e2e_steps):
-        e2e_step(k, k + 1 == e2e_steps)
+    for _ in range(e2e_steps):
+        e2e_step()
     torch.cuda.synchronize(dev)
     e2e_s = _max_over_ranks(world, time.perf_counter() - t0, dev)
     e2e_clk = e2e_clocks.stop()
@@ -361,6 +376,31 @@ def run_gpu(args, world, rank, local):
 
     w2_final = records[-1][2]
     sim.close()
+
+    # the two smaller growth workloads, timed as whole runs from t = 0: the
+    # launch-bound L = 256 run (1000 sweeps, 20 samples) and the L2-resident
+    # L = 2^14 run (10^4 sweeps, 40 samples; two 32 MiB ping-pong planes)
+    small = {}
+    for name, (Ls, T, ns, sd) in (("growth_L256", (256, 1000, 20, 1)),
+                                  ("growth_L16384", (16384, 10000, 40, 7))):
+        rec = growth_line(okz, Ls, T, ns, sd + rank)
+        rate = rec["value"] * 1e9
+        rec["roofline"] = {"bound": "alu", "achieved": ALU_OPS_PER_SITE_SWEEP["parity"] * rate / 1e12,
+                           "peak": peak_meas["value"], "unit": "Tops/s",
+                           "frac": ALU_OPS_PER_SITE_SWEEP["parity"] * rate / 1e12
+                           / peak_meas["value"],
+                           "note": "whole run incl. the W^2 samples, against the measured "
+                                   "ALU-pipe rate"}
+        if Ls == 16384:
+            rec["l2"] = "L2-resident (2 x 32 MiB parity planes < 126 MiB L2): not an HBM case"
+        small[name] = rec
+    # the batched and served forms (compact records; --workload batched /
+    # served print the same as lines of their own)
+    batched = served = None
+    if not args.no_forms:
+        batched = batched_record(okz, args.budget_frac, args.plain_stride, rank, world)
+        from paper_1110_6745_gb300 import serve
+        served = serve.served_record(UNIT)
     if rank != 0:
         return
     line = {
@@ -380,26 +420,69 @@ def run_gpu(args, world, rank, local):
                      "traffic": traffic,
                      "kernel": ("parity_stream_kernel" if repr_name == "parity"
                                 else "sweep_stream_kernel"),
-                     "peak_kind": "derived: 152 SMs x 64 INT32 lanes x sampled SM clock",
+                     "peak_kind": "measured: okz_alu_peak on this GPU, scaled to the timed "
+                                  "region's SM clock",
+                     "peak_measured": peak_meas,
+                     "peak_derived": N_SMS * ALU_LANES_PER_SM * sm_mhz * 1e6 / 1e12,
                      "ops_per_launch": alu_ops, "sweeps_per_launch": fuse,
                      "words_per_thread": wpt, "launch_ms": per_launch_s * 1e3},
         "roofline_hbm": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "bytes_per_launch": alg_bytes, "peak_kind": peak_kind},
         "sweep_gups": N * fuse / per_launch_s / 1e9,
-        "slope_roofline_frac": (N * fuse / per_launch_s) * 0.5 / (peak * 1e9),
+        # not a roofline: the rate the paper's two-plane encoding (0.5 B per
+        # site and sweep) would need from HBM at this attempt rate
+        "slope_plane_equiv_bw_frac": (N * fuse / per_launch_s) * 0.5 / (peak * 1e9),
         "gpu_launches": launches,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": e2e_steps, "clocks": e2e_clk,
                 "ms_per_step": e2e_s / e2e_steps * 1e3,
-                "pipelining": "H2D of step k+1 on a copy stream during step k"},
+                "path": "okz_restore(pinned host planes) + okz_sweep + okz_width2, "
+                        "synchronous, no overlap between steps"},
         "w2_final": w2_final,
         "clocks": clk,
+        "smaller_growth_workloads": small,
     }
+    if batched is not None:
+        line["batched"] = batched
+        line["served"] = served
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
         line["cpu_baseline_serial"] = cpu_serial_baseline()
     print(json.dumps(line), flush=True)
+
+
+def growth_line(okz, L, T, nsamp, seed, reps=3):
+    """A whole growth run as the paper times it (Sec. III): the striped start
+    swept to n log-spaced sample times over T sweeps, the exact W^2 taken at
+    every sample (host-synchronous: each sample's sums are read back). Timed
+    on the host clock from t = 0, best of `reps` runs after one untimed run.
+    Returns attempts/s and the time per run and per sample."""
+    from paper_1110_6745_gb300.analysis import sample_times
+    times = sample_times(T, nsamp)
+    best, info, w2_last = None, None, None
+    for rep in range(reps + 1):
+        with okz.Simulation(L, 1.0, 0.0, seed=seed) as sim:
+            sim.width2()  # the lattice is initialised before the clock starts
+            t0 = time.perf_counter()
+            done = 0
+            for t in times:
+                sim.sweep(t - done)
+                done = t
+                w2_last = sim.width2()[2]
+            dt = time.perf_counter() - t0
+            info = sim.info()
+        if rep > 0 and (best is None or dt < best):
+            best = dt
+    return {"value": L * L * T / best / 1e9, "unit": UNIT, "L": L, "sweeps": T,
+            "samples": len(times), "ms_per_run": best * 1e3,
+            "us_per_sample": best * 1e6 / len(times), "w2_final": w2_last,
+            "kernel": {1: "slope plain", 2: "slope stream", 3: "parity plain",
+                       4: "parity stream"}[info.kernel],
+            "words_per_thread": info.words_per_thread, "sweeps_per_pass": info.sweeps_per_pass,
+            "graph_chunk": info.graph_chunk, "graph_replays_per_run": info.graph_replays,
+            "timing": "host clock around the whole run (sweeps and synchronous W^2 "
+                      "samples), best of %d" % reps}
 
 
 def replica_mix(n=4096, seed=2026):
@@ -414,78 +497,87 @@ def replica_mix(n=4096, seed=2026):
     return L, T, seeds
 
 
-def run_batched(args, world, rank, local):
-    """4096 independent replicas in one graph-captured persistent launch, against
-    per-replica launches of the plain kernel on the same GPU."""
+def batched_record(okz, frac, plain_stride, rank=0, world=1):
+    """The batched workload: all 4096 replicas in one graph-captured
+    persistent launch (tiling autotuned first) at budgets ceil(4 L^1.61)/frac,
+    against per-replica plain launches (the in-place parity kernel, one
+    okz_sim per replica, every launch enqueued back to back on one stream and
+    one synchronisation at the end) of every plain_stride-th replica at the
+    same budgets. Both rates are aggregate attempts per second."""
     import numpy as np
+    import torch
+    L, T, seeds = replica_mix()
+    n = len(L)
+    budgets = np.maximum(1, T // frac)
+    b = okz.Batch(L, [0.95] * n, [0.05] * n, [int(x) + rank for x in seeds])
+    tune = b.autotune(probe_sweeps=2)
+    st = torch.cuda.ExternalStream(b.stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    _barrier(world)
+    e0.record(st)
+    b.run(budgets)
+    b.sync()
+    W2, sk, ku = b.stats()
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = _max_over_ranks(world, e0.elapsed_time(e1))
+    tiling = b.tiling()
+    b.close()
+    attempts = float(np.sum(L.astype(np.float64) ** 2 * budgets))
+    batched = world * attempts / (ms / 1e3) / 1e9
+    # per-replica plain launches, same budgets, a strided subset of the mix
+    idx = list(range(0, n, plain_stride))
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        sims = [okz.Simulation(int(L[r]), 0.95, 0.05, seed=int(seeds[r]) + rank,
+                               kernel=okz.OKZ_KERNEL_PARITY_PLAIN, torch_buffer=True)
+                for r in idx]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k, r in enumerate(idx):
+        sims[k].sweep(int(budgets[r]))
+    torch.cuda.synchronize()
+    plain_s = time.perf_counter() - t0
+    plain_attempts = float(np.sum(L[idx].astype(np.float64) ** 2 * budgets[idx]))
+    plain = plain_attempts / plain_s / 1e9
+    for s_ in sims:
+        s_.close()
+    # algorithmic ALU-pipe work of the k = 32 mix is not fixed per attempt
+    # (the random levels are drawn lazily), so no roofline fraction is given
+    return {"value": batched, "unit": UNIT, "ms": ms, "replicas": n, "attempts": attempts,
+            "budgets": "ceil(4 L^1.61)/%d sweeps" % frac,
+            "tiling": {"threads": tiling[0], "smem_bytes": tiling[1], "grid": tiling[2]},
+            "autotune": tune,
+            "per_replica_plain": {"value": plain, "unit": UNIT, "replicas": len(idx),
+                                  "budgets": "the same",
+                                  "kernel": "parity plain (graph-replayed sweeps), one okz_sim "
+                                            "per replica, launches back to back on one stream, "
+                                            "one synchronisation at the end",
+                                  "seconds": plain_s},
+            "batched_over_plain": batched / plain,
+            "w2_mean_by_L": {int(l): float(np.nanmean(W2[L == l])) for l in np.unique(L)}}
+
+
+def run_batched(args, world, rank, local):
+    """--workload batched: the batched line of its own."""
     import torch
 
     import paper_1110_6745_gb300 as okz
-
     torch.cuda.set_device(local)
-    L, T, seeds = replica_mix()
-    n = len(L)
-    frac = args.budget_frac
-    budgets = np.maximum(1, T // frac)
-    small = np.maximum(1, T // args.baseline_frac)
-
-    def batched(sw):
-        b = okz.Batch(L, [0.95] * n, [0.05] * n, [int(x) + rank for x in seeds])
-        b.autotune(probe_sweeps=2)
-        st = torch.cuda.ExternalStream(b.stream)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        _barrier(world)
-        e0.record(st)
-        b.run(sw)
-        b.sync()
-        W2, sk, ku = b.stats()
-        e1.record(st)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
-        tiling = b.tiling()
-        b.close()
-        return ms, W2, tiling
-
-    ms, W2, tiling = batched(budgets)
-    ms = _max_over_ranks(world, ms)
-    attempts = float(np.sum(L.astype(np.float64) ** 2 * budgets))
-    value = world * attempts / (ms / 1e3) / 1e9
-    ms_small, _, _ = batched(small)
-    batched_small = float(np.sum(L.astype(np.float64) ** 2 * small)) / (ms_small / 1e3) / 1e9
-
-    # per-replica launches of the plain (parity-plane, in-place) kernel
-    sims = [okz.Simulation(int(L[r]), 0.95, 0.05, seed=int(seeds[r]) + rank,
-                           kernel=okz.OKZ_KERNEL_PARITY_PLAIN) for r in range(n)]
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for r in range(n):
-        sims[r].sweep(int(small[r]))
-        sims[r].synchronize()
-    plain_s = time.perf_counter() - t0
-    plain = float(np.sum(L.astype(np.float64) ** 2 * small)) / plain_s / 1e9
-    check = [int(r) for r in np.argsort(L)[:: n // 16]]
-    for s_ in sims:
-        s_.close()
+    rec = batched_record(okz, args.budget_frac, args.plain_stride, rank, world)
     if rank != 0:
         return
     line = {
-        "metric": "aggregate site-update attempts/s, batched replicas", "value": value,
-        "unit": UNIT, "n_gpus": world, "steps": 1, "warmup": 0, "ms_per_step": ms,
+        "metric": "aggregate site-update attempts/s, batched replicas", "value": rec["value"],
+        "unit": UNIT, "n_gpus": world, "steps": 1, "warmup": 0, "ms_per_step": rec["ms"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic", "impl": "okz-batch",
         "config": {"workload": "4096 replicas, L = 2^e, e ~ U{6..11} (PCG64 2026), p=0.95 "
                                "q=0.05 s_sel=1/2, seeds 1000+r, striped start, budgets "
-                               "ceil(4 L^1.61)/%d sweeps; final W^2, skewness, kurtosis" % frac,
-                   "replicas": n, "attempts": attempts,
-                   "tiling": {"threads": tiling[0], "smem_bytes": tiling[1], "grid": tiling[2]}},
-        "per_replica_plain": {"value": plain, "unit": UNIT,
-                              "budgets": "ceil(4 L^1.61)/%d" % args.baseline_frac,
-                              "kernel": "parity plain, one okz_sim per replica, sequential"},
-        "batched_same_budgets": {"value": batched_small, "unit": UNIT},
-        "batched_over_plain": batched_small / plain,
-        "w2_mean_by_L": {int(l): float(np.nanmean(W2[L == l])) for l in np.unique(L)},
-    }
+                               "ceil(4 L^1.61)/%d sweeps; final W^2, skewness, kurtosis"
+                               % args.budget_frac}}
+    line.update({k: v for k, v in rec.items() if k not in ("value", "unit")})
     print(json.dumps(line), flush=True)
 
 
@@ -687,6 +779,8 @@ def main():
     ap.add_argument("--impl", default="okz", choices=["okz", "reference"])
     ap.add_argument("--L", type=int, default=L_DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="growth line only: skip the batched and served records")
     ap.add_argument("--kernel", default="auto", choices=sorted(KERNELS))
     ap.add_argument("--wpt", type=int, default=0, help="words per thread (0 = library choice)")
     ap.add_argument("--fuse", type=int, default=0, help="sweeps per launch (0 = library choice)")
@@ -694,8 +788,8 @@ def main():
                     choices=["growth", "batched", "served", "rs", "spectrum", "steady"])
     ap.add_argument("--budget-frac", type=int, default=64,
                     help="batched: run ceil(4 L^1.61)/frac sweeps per replica")
-    ap.add_argument("--baseline-frac", type=int, default=2048,
-                    help="batched: budgets of the per-replica comparison")
+    ap.add_argument("--plain-stride", type=int, default=16,
+                    help="batched: time the per-replica plain launches on every n-th replica")
     args = ap.parse_args()
     world, rank, local = _dist_init(args)
     if args.impl == "reference":

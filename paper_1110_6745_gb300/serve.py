@@ -266,47 +266,64 @@ def run_alone(r):
         return Sk, sim.info().H0, W2
 
 
-def bench(args, world, rank, local, unit):
-    """bench.py --workload served: 10^4 Poisson requests at 200/s."""
-    import json
-
-    import torch
-    torch.cuda.set_device(local)
-    reqs = poisson_requests()
+def served_record(unit, n=10000, rate=200.0, alone_sample=200):
+    """The served workload (n Poisson requests at `rate` per second) through
+    one Server; aggregate attempts per second over the makespan, latency
+    percentiles (overall and per L), whether the offered load was sustained,
+    and the same requests run alone one after another on a sample."""
+    reqs = poisson_requests(n=n, rate=rate)
     srv = Server()
     res = srv.run(reqs)
     lat = np.array([res[r.rid].latency for r in reqs])
     attempts = sum(float(r.L) ** 2 * r.budget for r in reqs)
     value = attempts / srv.makespan / 1e9
-    # per-request runs on their own, one after another, on a sample
-    sample = reqs[:: max(1, len(reqs) // 200)]
+    arrivals_s = max(r.arrival for r in reqs)
+    sample = reqs[:: max(1, len(reqs) // alone_sample)]
     t0 = time.perf_counter()
     for r in sample:
         run_alone(r)
     alone_s = time.perf_counter() - t0
     alone = sum(float(r.L) ** 2 * r.budget for r in sample) / alone_s / 1e9
+    tick = srv.tick_sweeps
+    equal = srv.equal_ticks
     srv.close()
-    if rank != 0:
-        return
-    line = {
-        "metric": "aggregate site-update attempts/s, served requests", "value": value,
-        "unit": unit, "n_gpus": world, "steps": 1, "warmup": 0,
-        "ms_per_step": srv.makespan * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "u32", "data": "synthetic", "impl": "okz-serve",
-        "config": {"workload": "10^4 requests, Poisson 200/s (PCG64 2027), L = 2^e, "
-                               "e ~ U{7..13}, p ~ U{1, 0.75, 0.5}, q = 1 - p, budgets "
-                               "round(10^U(2,4)) sweeps, admitted by slot and HBM footprint",
-                   "requests": len(reqs), "tick_sweeps": srv.tick_sweeps,
-                   "tick": ("equal site updates per slot (tick_sweeps sweeps of L = 2048)"
-                            if srv.equal_ticks else "tick_sweeps sweeps per slot")},
+    return {
+        "value": value, "unit": unit, "requests": len(reqs), "makespan_s": srv.makespan,
+        "offered": attempts / arrivals_s / 1e9, "arrival_window_s": arrivals_s,
+        "sustained": bool(srv.makespan <= 1.1 * arrivals_s),
         "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                       "max": float(lat.max())},
         "latency_by_L_s": {str(L): [float(np.percentile(lat[m], 50)),
                                     float(np.percentile(lat[m], 99))]
                            for L in sorted(set(r.L for r in reqs))
                            for m in [np.array([r.L == L for r in reqs])]},
-        "makespan_s": srv.makespan,
-        "per_request_alone": {"value": alone, "unit": unit, "sample": len(sample)},
+        "per_request_alone": {"value": alone, "unit": unit, "sample": len(sample),
+                              "seconds": alone_s},
         "served_over_alone": value / alone,
+        "tick_sweeps": tick,
+        "tick": ("equal site updates per slot (tick_sweeps sweeps of L = 2048)"
+                 if equal else "tick_sweeps sweeps per slot"),
     }
+
+
+def bench(args, world, rank, local, unit):
+    """bench.py --workload served: 10^4 Poisson requests at 200/s."""
+    import json
+
+    import torch
+    torch.cuda.set_device(local)
+    rec = served_record(unit)
+    if rank != 0:
+        return
+    line = {
+        "metric": "aggregate site-update attempts/s, served requests", "value": rec["value"],
+        "unit": unit, "n_gpus": world, "steps": 1, "warmup": 0,
+        "ms_per_step": rec["makespan_s"] * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic", "impl": "okz-serve",
+        "config": {"workload": "10^4 requests, Poisson 200/s (PCG64 2027), L = 2^e, "
+                               "e ~ U{7..13}, p ~ U{1, 0.75, 0.5}, q = 1 - p, budgets "
+                               "round(10^U(2,4)) sweeps, admitted by slot and HBM footprint",
+                   "requests": rec["requests"]},
+    }
+    line.update({k: v for k, v in rec.items() if k not in ("value", "unit")})
     print(json.dumps(line), flush=True)
