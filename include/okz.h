@@ -255,6 +255,23 @@ okz_status okz_state(okz_sim *sim, uint32_t *planes_out, int out_is_device,
 okz_status okz_restore(okz_sim *sim, const uint32_t *planes, int in_is_device,
                        int64_t H0, uint64_t t);
 
+/* okz_tune_stream -- the paper has no counterpart to this entry point (the
+ * tiling of the update is this build's). Autotuner of the stream kernels'
+ * launch shape for one workload: for every valid words_per_thread (4, 8, 16)
+ * and sweeps_per_pass (1, 2) it creates a scratch simulation of prm (kernel
+ * STREAM or PARITY_STREAM; AUTO means PARITY_STREAM), runs 4 sweeps, then
+ * times probe_sweeps (>= 2) sweeps with CUDA events, and keeps the fastest
+ * per sweep. The choice is remembered for (device, L, kernel, acceptance
+ * mode: k = 1 with minima only, other k <= 1, k >= 2) and used by every later
+ * okz_create / okz_create_ex that leaves both words_per_thread and
+ * sweeps_per_pass automatic (0). Results are bit-identical for every tiling,
+ * so tuning never changes a result. Writes the choice and its time per sweep
+ * (any output may be NULL). Synchronizing; each scratch simulation holds
+ * okz_device_bytes(L) for its run. Errors: EINVAL, EUNSUPPORTED (L outside the
+ * stream kernels' range), ENOMEM, ECUDA, ETIMEOUT. */
+okz_status okz_tune_stream(const okz_params *prm, int32_t probe_sweeps, int32_t *wpt_out,
+                           int32_t *fuse_out, double *ms_per_sweep);
+
 /* Fills *info. Synchronizing (H0 lives on the device). */
 okz_status okz_get_info(okz_sim *sim, okz_info *info);
 

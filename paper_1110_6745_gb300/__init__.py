@@ -74,6 +74,8 @@ _SIGS = {
     "okz_selftest_wait_timeout": (_c.c_int, [_vp]),
     "okz_alu_peak": (_c.c_int, [_vp, _c.c_int32, _c.POINTER(_c.c_double),
                                 _c.POINTER(_c.c_double)]),
+    "okz_tune_stream": (_c.c_int, [_c.POINTER(okz_params), _c.c_int32, _c.POINTER(_c.c_int32),
+                                   _c.POINTER(_c.c_int32), _c.POINTER(_c.c_double)]),
     "okz_moments_fetch": (_c.c_int, [_vp, _c.POINTER(okz_i128), _c.POINTER(_c.c_double),
                                _c.POINTER(_c.c_double), _c.POINTER(_c.c_double)]),
     "okz_psd": (_c.c_int, [_vp, _vp]),
@@ -204,6 +206,20 @@ def okz_alu_peak(stream=None, iters=20000):
     _check(lib().okz_alu_peak(stream, int(iters), ctypes.byref(ops), ctypes.byref(ms)),
            "okz_alu_peak")
     return ops.value, ms.value
+
+
+def okz_tune_stream(L, p, q, s_sel=0.5, k_max=32, kernel=0, probe_sweeps=8):
+    """Autotunes the stream kernels' (words per thread, sweeps per pass) for
+    this workload; later Simulations with automatic tiling use the choice.
+    -> (words_per_thread, sweeps_per_pass, ms per sweep)."""
+    prm = okz_params()
+    lib().okz_params_init(ctypes.byref(prm))
+    prm.L, prm.p, prm.q, prm.s_sel, prm.k_max, prm.kernel = int(L), float(p), float(q), \
+        float(s_sel), int(k_max), int(kernel)
+    w, f, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+    _check(lib().okz_tune_stream(ctypes.byref(prm), int(probe_sweeps), ctypes.byref(w),
+                                 ctypes.byref(f), ctypes.byref(ms)), "okz_tune_stream")
+    return w.value, f.value, ms.value
 
 
 def okz_moments_enqueue(h):

@@ -122,6 +122,45 @@ static okz_status check_L(int64_t L) {
   return OKZ_OK;
 }
 
+// Kernel mode of the stream kernels for thresholds (k, P, Q): 0 = k = 1 with
+// only minima moving at one random level (P < 2^k, Q = 0), 1 = other k <= 1,
+// 2 = k >= 2 (lazily drawn levels).
+static int stream_mode(int k, uint64_t P, uint64_t Q) {
+  if (k >= 2) return 2;
+  const uint64_t full = 1ull << k;
+  const bool half = P != 0 && P < full && Q == 0;
+  return half ? 0 : 1;
+}
+
+// Tilings chosen by okz_tune_stream, per (device, L, kernel, mode).
+struct TuneKey {
+  int dev;
+  int64_t L;
+  int kernel, mode;
+  bool operator<(const TuneKey &o) const {
+    if (dev != o.dev) return dev < o.dev;
+    if (L != o.L) return L < o.L;
+    if (kernel != o.kernel) return kernel < o.kernel;
+    return mode < o.mode;
+  }
+};
+static std::mutex g_tune_mu;
+static std::map<TuneKey, std::pair<int, int>> g_tuned;
+
+static bool tuned_tiling(int64_t L, int kernel, int mode, int *wpt, int *fuse) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  auto it = g_tuned.find(TuneKey{dev, L, kernel, mode});
+  if (it == g_tuned.end()) return false;
+  *wpt = it->second.first;
+  *fuse = it->second.second;
+  return true;
+}
+
 }  // namespace okz
 
 using namespace okz;
@@ -215,6 +254,13 @@ okz_status okz_create_ex(const okz_params *prm, void *dev_buf, size_t bytes, voi
     return OKZ_EUNSUPPORTED;
   }
   int wpt = prm->words_per_thread, fuse = prm->sweeps_per_pass;
+  if (streamed && wpt == 0 && fuse == 0) {  // a tiling okz_tune_stream measured best
+    int tw = 0, tf = 0;
+    if (tuned_tiling(prm->L, kernel, stream_mode(k, P, Q), &tw, &tf)) {
+      wpt = tw;
+      fuse = tf;
+    }
+  }
   if (streamed) {
     // defaults measured on GB300. Slope planes: 8 words per thread where the
     // row allows it, one sweep per pass. Parity plane with one random level
@@ -794,6 +840,82 @@ okz_status okz_get_info(okz_sim *sim, okz_info *info) {
   info->device_bytes = sim->lay.total;
   info->words_per_thread = sim->wpt;
   info->sweeps_per_pass = sim->fuse;
+  return OKZ_OK;
+}
+
+okz_status okz_tune_stream(const okz_params *prm, int32_t probe_sweeps, int32_t *wpt_out,
+                           int32_t *fuse_out, double *ms_per_sweep) {
+  if (!prm || probe_sweeps < 2) {
+    set_error("okz_tune_stream: null parameters or probe_sweeps < 2");
+    return OKZ_EINVAL;
+  }
+  okz_status st = check_L(prm->L);
+  if (st != OKZ_OK) return st;
+  int32_t k;
+  uint64_t P, Q;
+  st = okz_thresholds(prm->p, prm->q, prm->s_sel, prm->k_max, &k, &P, &Q);
+  if (st != OKZ_OK) return st;
+  int kernel = prm->kernel;
+  if (kernel == OKZ_KERNEL_AUTO && stream_kernel_supports(prm->L)) kernel = OKZ_KERNEL_PARITY_STREAM;
+  if ((kernel != OKZ_KERNEL_STREAM && kernel != OKZ_KERNEL_PARITY_STREAM) ||
+      !stream_kernel_supports(prm->L)) {
+    set_error("okz_tune_stream: the stream kernels need L % 4096 == 0 and L <= 131072");
+    return OKZ_EUNSUPPORTED;
+  }
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  double best = 1e300;
+  int bw = 0, bf = 0;
+  const int wpts[3] = {4, 8, 16};
+  for (int wi = 0; wi < 3; ++wi)
+    for (int f = 1; f <= 2; ++f) {
+      const int w = wpts[wi];
+      const bool ok = kernel == OKZ_KERNEL_PARITY_STREAM ? parity_wpt_valid(prm->L, w)
+                                                         : stream_wpt_valid(prm->L, w);
+      if (!ok) continue;
+      okz_params q = *prm;
+      q.kernel = kernel;
+      q.words_per_thread = w;
+      q.sweeps_per_pass = f;
+      okz_sim *sim = nullptr;
+      st = okz_create_ex(&q, nullptr, 0, nullptr, &sim);
+      if (st != OKZ_OK) return st;
+      cudaEvent_t e0 = nullptr, e1 = nullptr;
+      e = cudaEventCreate(&e0);
+      if (e == cudaSuccess) e = cudaEventCreate(&e1);
+      float ms = 0.0f;
+      if (e == cudaSuccess) {
+        // past the striped start (its first sweeps move every site), then timed
+        okz_status s2 = okz_sweep(sim, 4);
+        if (s2 == OKZ_OK) e = cudaEventRecord(e0, sim->stream);
+        if (s2 == OKZ_OK && e == cudaSuccess) s2 = okz_sweep(sim, probe_sweeps);
+        if (s2 == OKZ_OK && e == cudaSuccess) e = cudaEventRecord(e1, sim->stream);
+        if (s2 == OKZ_OK && e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (s2 == OKZ_OK && e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (s2 != OKZ_OK) st = s2;
+      }
+      if (e0) cudaEventDestroy(e0);
+      if (e1) cudaEventDestroy(e1);
+      const okz_status s3 = sync_and_check(sim);
+      okz_destroy(sim);
+      if (st != OKZ_OK) return st;
+      if (e != cudaSuccess) return cuda_fail(e, "okz_tune_stream timing");
+      if (s3 != OKZ_OK) return s3;
+      const double per = ms / probe_sweeps;
+      if (per < best) {
+        best = per;
+        bw = w;
+        bf = f;
+      }
+    }
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tuned[TuneKey{dev, prm->L, kernel, stream_mode(k, P, Q)}] = {bw, bf};
+  }
+  if (wpt_out) *wpt_out = bw;
+  if (fuse_out) *fuse_out = bf;
+  if (ms_per_sweep) *ms_per_sweep = best;
   return OKZ_OK;
 }
 

@@ -89,3 +89,13 @@ def test_alu_peak_rejects_bad_arguments(okz):
     with pytest.raises(okz.OkzError) as e:
         okz.okz_alu_peak(None, 0)
     assert e.value.status == okz.OKZ_EINVAL
+
+
+def test_tune_stream_rejects_bad_requests(okz):
+    """okz_tune_stream checks its arguments before touching the device."""
+    with pytest.raises(okz.OkzError) as e:
+        okz.okz_tune_stream(8192, 1.0, 0.0, probe_sweeps=1)
+    assert e.value.status == okz.OKZ_EINVAL
+    with pytest.raises(okz.OkzError) as e:
+        okz.okz_tune_stream(2048, 1.0, 0.0)  # below the stream kernels' range
+    assert e.value.status == okz.OKZ_EUNSUPPORTED

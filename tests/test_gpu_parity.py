@@ -152,6 +152,34 @@ def test_parity_stream_wpt16_long_run(okz, L, p, q, fuse):
     b.close()
 
 
+@pytest.mark.parametrize("L,p,q,kernel", [(16384, 1.0, 0.0, 4), (8192, 0.75, 0.25, 4),
+                                          (16384, 1.0, 1.0, 4), (8192, 1.0, 0.0, 2)])
+def test_tuned_tiling_is_bit_identical(okz, orc, L, p, q, kernel):
+    """okz_tune_stream's choice is used by simulations with automatic tiling
+    and gives the same lattice as the untuned default and, at L = 8192, as the
+    oracle."""
+    base = okz.Simulation(L, p, q, seed=61, kernel=kernel)
+    default = (base.wpt, base.fuse)
+    base.close()
+    wpt, fuse, ms = okz.okz_tune_stream(L, p, q, kernel=kernel, probe_sweeps=4)
+    assert ms > 0 and (wpt, fuse) != (0, 0)
+    a = okz.Simulation(L, p, q, seed=61, kernel=kernel)
+    assert (a.wpt, a.fuse) == (wpt, fuse)
+    b = okz.Simulation(L, p, q, seed=61, kernel=kernel, words_per_thread=default[0],
+                       sweeps_per_pass=default[1])
+    a.sweep(9)
+    b.sweep(9)
+    pa, ha, ta = a.state()
+    pb, hb, tb = b.state()
+    assert np.array_equal(pa, pb) and (ha, ta) == (hb, tb)
+    if L == 8192:
+        ref = orc.Sim(L, p, q, 61)
+        ref.sweep(9)
+        _compare(a, ref)
+    a.close()
+    b.close()
+
+
 def test_wpt16_rejected_where_invalid(okz):
     """16 words per thread needs L % 16384 == 0 and the parity stream kernel."""
     for L, kernel in ((8192, okz.OKZ_KERNEL_PARITY_STREAM), (12288, okz.OKZ_KERNEL_PARITY_STREAM),
