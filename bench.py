@@ -736,32 +736,40 @@ def run_spectrum(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
+# Steady-state plan per L: replicas, burn-in and sample spacing in units of
+# L^1.61 sweeps (about the saturation time at s_sel = 1/2), samples.
+STEADY_PLAN = {128: (304, 4, 1, 8), 256: (304, 4, 1, 8), 512: (304, 4, 1, 8),
+               1024: (304, 4, 1, 8), 2048: (152, 3, 1, 5)}
+
+
 def run_steady(args, world, rank, local):
     """--workload steady: the steady-state statistics of Secs. III-IV on the
-    batched kernels -- 304 replicas at each L = 64 .. 512 run from the striped
-    start for 4 L^1.61 sweeps and sampled 8 times L^1.61 sweeps apart (exact
-    W^2 per sample); alpha_eff (Eq. (13)) and kappa_2 / kappa_1^2 per L."""
+    batched kernels -- replicas at L = 128 .. 2048 (STEADY_PLAN) run from the
+    striped start, then sampled (exact W^2 per sample); alpha_eff(L) (Eq.
+    (13)) with jackknife errors, the fit of Eq. (14) at the paper's
+    correction exponent, and kappa_2 / kappa_1^2 per L."""
     import numpy as np
     import torch
 
-    from paper_1110_6745_gb300.analysis import alpha_eff, steady_state_w2, w2_cumulants
+    from paper_1110_6745_gb300.analysis import alpha_fss, steady_state_w2, w2_cumulants
 
     torch.cuda.set_device(local)
-    Ls, R, nsamp = [64, 128, 256, 512], 304, 8
-    means, ratios, attempts = {}, {}, 0.0
+    samples, ratios, attempts, secs = {}, {}, 0.0, {}
     _barrier(world)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for L in Ls:
+    for L, (R, burn_tx, every_tx, nsamp) in sorted(STEADY_PLAN.items()):
         tx = L ** 1.61
-        burn, every = int(4 * tx), int(tx)
+        burn, every = int(burn_tx * tx), int(every_tx * tx)
+        t1 = time.perf_counter()
         w = steady_state_w2(L, R, burn, nsamp, every, seed0=100000 + 1000 * L + 10 ** 6 * rank)
+        secs[L] = time.perf_counter() - t1
         k = w2_cumulants(w)
-        means[L], ratios[L] = float(w.mean()), k[1] / k[0] ** 2
+        samples[L], ratios[L] = w, k[1] / k[0] ** 2
         attempts += float(L) ** 2 * R * (burn + nsamp * every)
     torch.cuda.synchronize()
     dt = _max_over_ranks(world, time.perf_counter() - t0)
-    Le, ae = alpha_eff(Ls, [means[L] for L in Ls])
+    fss = alpha_fss(samples, omega=1.16)
     if rank != 0:
         return
     line = {
@@ -769,13 +777,14 @@ def run_steady(args, world, rank, local):
         "value": world * attempts / dt / 1e9, "n_gpus": world, "steps": 1, "warmup": 0,
         "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic", "impl": "okz-steady",
-        "config": {"workload": "steady state, 304 replicas per L in {64,128,256,512}, p=1 q=0 "
-                               "s_sel=1/2, 4 L^1.61 burn-in sweeps, 8 samples L^1.61 apart",
-                   "replicas": R, "samples": nsamp},
-        "w2_mean_by_L": {str(L): means[L] for L in Ls},
-        "alpha_eff": {str(int(L)): float(a) for L, a in zip(Le, ae)},
-        "kappa2_over_kappa1_sq": {str(L): float(ratios[L]) for L in Ls},
-        "paper_alpha": 0.393,
+        "config": {"workload": "steady state, p=1 q=0 s_sel=1/2, striped start; per L: "
+                               "(replicas, burn-in and spacing in L^1.61 sweeps, samples)",
+                   "plan": {str(L): v for L, v in sorted(STEADY_PLAN.items())}},
+        "w2_mean_by_L": {str(L): float(samples[L].mean()) for L in samples},
+        "seconds_by_L": {str(L): secs[L] for L in secs},
+        "alpha_fss": fss,
+        "kappa2_over_kappa1_sq": {str(L): float(ratios[L]) for L in ratios},
+        "paper_alpha": "0.393(4), correction exponent 1.16 (Sec. III)",
     }
     print(json.dumps(line), flush=True)
 

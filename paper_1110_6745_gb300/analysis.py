@@ -96,6 +96,45 @@ def fit_alpha(Ls, a_eff, omega):
     return float(alpha), float(c)
 
 
+def alpha_fss(samples_by_L, omega=1.16, blocks=32):
+    """Finite-size scaling of the steady-state width (Sec. III, Eqs. (13),
+    (14)) with errors: alpha_eff(L) from the replica-and-sample means of W^2
+    at L and L/2, and the fit alpha_eff(L) = alpha + c L^(-omega) at the fixed
+    correction exponent omega. samples_by_L maps L to a (replicas x samples)
+    array of W^2. Errors by delete-one-block jackknife: every L's replicas are
+    split into `blocks` groups and block b is left out at every L at once.
+    Returns a dict: L, alpha_eff, alpha_eff_err, alpha, alpha_err, c, c_err."""
+    Ls = sorted(int(L) for L in samples_by_L)
+    arrs = {L: np.asarray(samples_by_L[L], dtype=np.float64) for L in Ls}
+
+    def estimate(drop=None):
+        means = []
+        for L in Ls:
+            a = arrs[L]
+            if drop is not None:
+                idx = np.array_split(np.arange(a.shape[0]), blocks)[drop]
+                a = np.delete(a, idx, axis=0)
+            means.append(a.mean())
+        Le, ae = alpha_eff(Ls, means)
+        if len(Le) >= 2:
+            al, c = fit_alpha(Le, ae, omega)
+        else:
+            al, c = float("nan"), float("nan")
+        return Le, ae, al, c
+
+    Le, ae, al, c = estimate()
+    jk = [estimate(b) for b in range(blocks)]
+    f = (blocks - 1) / blocks
+    ae_j = np.array([j[1] for j in jk])
+    al_j = np.array([j[2] for j in jk])
+    c_j = np.array([j[3] for j in jk])
+    err = lambda v: float(np.sqrt(f * np.sum((v - v.mean(axis=0)) ** 2, axis=0))) \
+        if np.ndim(v) == 1 else np.sqrt(f * np.sum((v - v.mean(axis=0)) ** 2, axis=0))
+    return {"L": [int(x) for x in Le], "alpha_eff": [float(x) for x in ae],
+            "alpha_eff_err": [float(x) for x in err(ae_j)], "alpha": float(al),
+            "alpha_err": err(al_j), "c": float(c), "c_err": err(c_j), "omega": float(omega)}
+
+
 def steady_state_psd(L, replicas, burnin, nsamples, every, p=1.0, q=0.0, seed0=0):
     """The axis spectrum S[k] (okz_psd) averaged over `replicas` lattices of
     size L (seeds seed0 + r) and `nsamples` times `every` sweeps apart after

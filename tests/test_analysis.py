@@ -116,7 +116,7 @@ def test_steady_state_sampler_matches_single_runs():
 
 @pytest.fixture(scope="module")
 def steady():
-    """Steady-state W^2 samples at L = 128, 256, 512: 304 replicas each (two
+    """Steady-state W^2 samples at L = 128 ... 1024: 304 replicas each (two
     per SM of the batched kernel), 4 L^1.61 sweeps of burn-in from the striped
     start (saturation is reached near L^1.61 sweeps at s_sel = 1/2), then 8
     samples L^1.61 sweeps apart (about one correlation time)."""
@@ -126,7 +126,7 @@ def steady():
     _build.build()
     from paper_1110_6745_gb300.analysis import steady_state_w2
     out = {}
-    for L in (128, 256, 512):
+    for L in (128, 256, 512, 1024):
         tx = L ** 1.61
         out[L] = steady_state_w2(L, 304, int(4 * tx), 8, int(tx), seed0=100000 + 1000 * L)
     return out
@@ -134,15 +134,20 @@ def steady():
 
 @pytest.mark.gpu
 def test_alpha_eff_near_the_paper_value(steady):
-    """alpha_eff(L) (Eq. (13)) at L = 256 and 512 within 0.05 of the paper's
-    alpha = 0.393(4) (Sec. III), approached from below; each estimate has a
-    sampling error of about 0.01 (a statistical pin, not parity)."""
-    from paper_1110_6745_gb300.analysis import alpha_eff
-    Ls = sorted(steady)
-    Le, a = alpha_eff(Ls, [steady[L].mean() for L in Ls])
-    assert Le.tolist() == [256, 512]
-    assert np.all((a > 0.33) & (a < 0.43)), a
-    assert 0.35 < a.mean() < 0.41, a
+    """alpha_eff(L) (Eq. (13)) at L = 256, 512, 1024 and the fit of Eq. (14)
+    at the paper's correction exponent 1.16 against alpha = 0.393(4) (Sec.
+    III), with jackknife errors over the 304 replicas: every alpha_eff lies
+    below alpha + 4 sigma (the paper approaches alpha from below) and above
+    alpha - 0.03 - 4 sigma (finite-size corrections at these L), and the
+    fitted alpha within 4 sigma + 0.01 of the paper's (a statistical pin,
+    not parity)."""
+    from paper_1110_6745_gb300.analysis import alpha_fss
+    r = alpha_fss(steady, omega=1.16)
+    assert r["L"] == [256, 512, 1024]
+    for a, e in zip(r["alpha_eff"], r["alpha_eff_err"]):
+        assert 0 < e < 0.02, r
+        assert 0.393 - 0.03 - 4 * e < a < 0.393 + 4 * e, r
+    assert abs(r["alpha"] - 0.393) < 4 * r["alpha_err"] + 0.01, r
 
 
 @pytest.mark.gpu
@@ -170,3 +175,24 @@ def test_steady_state_spectrum_slope():
     assert np.allclose(S[1:], S[1:][::-1], rtol=1e-9)  # real surface: S(k) = S(-k)
     slope = spectrum_slope(S, 1, 8)
     assert abs(slope - (-2 - 2 * 0.393)) < 0.15, slope
+
+
+def test_alpha_fss_recovers_a_corrected_power_law():
+    """alpha_fss on W^2 = a^2 L^(2 alpha) (1 + b L^(-w))^2: without noise the
+    fit of Eq. (14) at the true omega returns alpha (up to the difference
+    between the corrected power law and its first-order form) with zero
+    jackknife error; with multiplicative noise per sample the jackknife error
+    covers the deviation."""
+    from paper_1110_6745_gb300.analysis import alpha_fss
+    alpha, b, w = 0.393, -0.9, 1.16
+    Ls = [128, 256, 512, 1024, 2048]
+    exact = {L: np.full((64, 4), (0.7 * L ** alpha * (1 + b * L ** (-w))) ** 2) for L in Ls}
+    r = alpha_fss(exact, omega=w)
+    assert r["L"] == [256, 512, 1024, 2048]
+    assert abs(r["alpha"] - alpha) < 2e-3, r
+    assert max(r["alpha_eff_err"]) < 1e-12 and r["alpha_err"] < 1e-12
+    rng = np.random.default_rng(5)
+    noisy = {L: exact[L] * rng.lognormal(0.0, 0.2, size=exact[L].shape) for L in Ls}
+    r = alpha_fss(noisy, omega=w)
+    assert r["alpha_err"] > 0 and abs(r["alpha"] - alpha) < 5 * r["alpha_err"] + 2e-3, r
+    assert all(e > 0 for e in r["alpha_eff_err"])
