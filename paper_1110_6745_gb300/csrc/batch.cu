@@ -7,10 +7,10 @@
 // item, stages the lattice in shared memory when it fits (else works on it in
 // global memory, where a 2^11 lattice stays L2-resident), runs the sweeps in
 // place -- a half-sweep updates only one sublattice and a move toggles only
-// the site's own bit, so a CTA barrier between half-sweeps is the only
-// synchronisation -- and writes the lattice, t and H0 back. Random draws use
-// the slot's own seed with the single-lattice counter layout, so every slot
-// evolves bit-identically to a simulation of its own.
+// the site's own bit, so CTA barriers between the half-sweeps of bands of
+// rows are the only synchronisation -- and writes the lattice, t and H0 back.
+// Random draws use the slot's own seed with the single-lattice counter
+// layout, so every slot evolves bit-identically to a simulation of its own.
 #include <cuda_runtime.h>
 
 #include "okz_batch_internal.h"
@@ -102,84 +102,156 @@ __device__ __forceinline__ void group_update(uint32_t *B, int L, int W, uint32_t
   }
 }
 
-// Level 0 of a group is the same in both half-sweeps of a sweep (a site is
-// active in one of them). CACHE = 1: keep the level-0 words drawn in the
-// first half-sweep in cw and mark bit cbit of cvalid; CACHE = 2: take them
-// from there in the second (draw them if the first did not).
-constexpr int kCacheGroups = 8;  // groups per thread up to which level 0 is kept
+// ---- band wavefront (lattices with L % 128 == 0) ----
+//
+// Every random level of R6 is keyed by (group, sweep, level), never by the
+// half-sweep, and a site is active in one half-sweep only: the levels a group
+// draws for its first-half candidates decide its second-half sites just as
+// well, as far as they go. So the first half-sweep of a group advances the
+// comparisons U < P and U < Q of all 128 sites, and the second half-sweep
+// starts from that state and draws only the levels beyond it (the first-half
+// loop runs to the warp's last undecided candidate, which usually leaves
+// none). Carrying the state needs the thread that did a group's first half to
+// do its second half too, one barrier later, which a band wavefront gives:
+// per band step of R rows, the first half of rows y0 .. y0+R-1, a barrier,
+// the second half of rows y0-1 .. y0+R-2, a barrier. That is the checkerboard
+// order (a first-half site reads only second-half neighbours, and those of
+// rows y0-1 and y0+R have not moved yet), with two rows held back: a band's
+// last row waits for the next band step (its state goes through shared
+// memory), and row 0 waits for the end of the sweep, after the first half of
+// row L-1, which reads it.
 
-// Acceptance of 4 words (lazy, bit-sliced U < P / U < Q) -> flips.
-template <int CACHE>
-__device__ __forceinline__ void accept4(const uint32_t mn[4], const uint32_t mx[4], uint32_t g,
-                                        uint32_t t, const uint32_t *rks, const Accept &acc,
-                                        uint32_t f[4], uint32_t *cw, uint32_t &cvalid,
-                                        uint32_t cbit) {
-  const uint64_t full = 1ull << acc.k;
-  uint32_t ltp[4], eqp[4], ltq[4], eqq[4];
+constexpr int kBandCols = (int)(kBatchMaxL / 128);  // 128-site groups per row, at most
+constexpr int kCarryWords = 9;                      // LT[4], EQ[4], next level
+
+// [0], [1]: a band's last row, by band parity; [2]: row 0.
+struct BandCarry {
+  uint32_t w[3][kCarryWords][kBandCols];
+};
+
+__device__ __forceinline__ void carry_put(BandCarry &bc, int b, uint32_t col, const uint32_t LT[4],
+                                          const uint32_t EQ[4], int m) {
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    ltp[j] = (acc.P >= full) ? mn[j] : 0u;
-    eqp[j] = (acc.P >= full || acc.P == 0) ? 0u : mn[j];
-    ltq[j] = (acc.Q >= full) ? mx[j] : 0u;
-    eqq[j] = (acc.Q >= full || acc.Q == 0) ? 0u : mx[j];
+    bc.w[b][j][col] = LT[j];
+    bc.w[b][4 + j][col] = EQ[j];
   }
-  for (int m = 0; m < acc.k; ++m) {
-    if (((eqp[0] | eqq[0]) | (eqp[1] | eqq[1]) | (eqp[2] | eqq[2]) | (eqp[3] | eqq[3])) == 0u)
-      break;
-    u32x4 rb;
-    if (CACHE == 2 && m == 0 && (cvalid & cbit)) {
-#pragma unroll
-      for (int j = 0; j < 4; ++j) rb.v[j] = cw[j];
-    } else {
-      rb = philox10_sm(g, 0u, t, (uint32_t)m, rks);
-      if (CACHE == 1 && m == 0) {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) cw[j] = rb.v[j];
-        cvalid |= cbit;
-      }
-    }
-    const uint32_t pb = (uint32_t)(acc.P >> (acc.k - 1 - m)) & 1u;
-    const uint32_t qb = (uint32_t)(acc.Q >> (acc.k - 1 - m)) & 1u;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      lt_step(rb.v[j], pb, ltp[j], eqp[j]);
-      lt_step(rb.v[j], qb, ltq[j], eqq[j]);
-    }
-  }
-#pragma unroll
-  for (int j = 0; j < 4; ++j) f[j] = ltp[j] | ltq[j];
+  bc.w[b][8][col] = (uint32_t)m;
 }
 
-// A group of 4 words inside one row (L % 128 == 0): 3 vector loads (row,
-// row below, row above), 2 neighbour words, 1 vector store. Whole-word
-// stores are safe: every bit another thread reads from these words sits on a
-// site this half-sweep does not move.
-template <bool POW2, int SP, int CACHE>
-__device__ __forceinline__ void row_group_update(uint32_t *B, int L, int W, uint32_t gpr,
-                                                 int lg_gpr, uint32_t g, uint32_t t,
-                                                 const uint32_t *rks, const Accept &acc,
-                                                 int &dH0, uint32_t *cw, uint32_t &cvalid,
-                                                 uint32_t cbit) {
-  constexpr int s = SP;
-  const uint32_t y = POW2 ? (g >> lg_gpr) : (g / gpr);
-  const uint32_t w0 = 4 * (g - y * gpr);
+__device__ __forceinline__ void carry_get(const BandCarry &bc, int b, uint32_t col, uint32_t LT[4],
+                                          uint32_t EQ[4], int &m) {
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    LT[j] = bc.w[b][j][col];
+    EQ[j] = bc.w[b][4 + j][col];
+  }
+  m = (int)bc.w[b][8][col];
+}
+
+// philox(g, 0, t, m) for the successive levels m of one group in one sweep:
+// the first two rounds depend on m only through c2 = hi(A g) ^ k1 ^ m, so the
+// rest of them is formed once per group (same rounds and keys as
+// philox10_sm).
+struct LevelPhilox {
+  uint32_t X, Z, V1, V3;
+};
+
+__device__ __forceinline__ LevelPhilox level_philox_init(uint32_t g, uint32_t t,
+                                                         const uint32_t *rks) {
+  const uint64_t pa = (uint64_t)kPhiloxMulA * g, pb = (uint64_t)kPhiloxMulB * t;
+  const uint32_t U0 = (uint32_t)(pb >> 32) ^ rks[0];  // round 0: c0, c1 from t only
+  const uint64_t pa1 = (uint64_t)kPhiloxMulA * U0;    // round 1: c2, c3 from g, t only
+  LevelPhilox lp;
+  lp.X = (uint32_t)(pa >> 32) ^ rks[1];
+  lp.Z = (uint32_t)(pa1 >> 32) ^ (uint32_t)pa ^ rks[3];
+  lp.V1 = (uint32_t)pb ^ rks[2];
+  lp.V3 = (uint32_t)pa1;
+  return lp;
+}
+
+__device__ __forceinline__ u32x4 level_philox(const LevelPhilox &lp, uint32_t m,
+                                              const uint32_t *__restrict__ rks) {
+  const uint64_t p1 = (uint64_t)kPhiloxMulB * (lp.X ^ m);
+  uint32_t c0 = (uint32_t)(p1 >> 32) ^ lp.V1, c1 = (uint32_t)p1, c2 = lp.Z, c3 = lp.V3;
+#pragma unroll
+  for (int r = 2; r < 10; ++r) {
+    uint32_t kx, ky;
+    asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];"
+                 : "=r"(kx), "=r"(ky)
+                 : "r"((uint32_t)__cvta_generic_to_shared(rks + 2 * r)));
+    const uint64_t pa = (uint64_t)kPhiloxMulA * c0;
+    const uint64_t pb = (uint64_t)kPhiloxMulB * c2;
+    const uint32_t n0 = (uint32_t)(pb >> 32) ^ c1 ^ kx;
+    const uint32_t n2 = (uint32_t)(pa >> 32) ^ c3 ^ ky;
+    c1 = (uint32_t)pb;
+    c3 = (uint32_t)pa;
+    c0 = n0;
+    c2 = n2;
+  }
+  u32x4 out;
+  out.v[0] = c0;
+  out.v[1] = c1;
+  out.v[2] = c2;
+  out.v[3] = c3;
+  return out;
+}
+
+// Thresholds as 32-bit words with level 0 at bit 31 (P < 2^k; a P of 0 or
+// 2^k never reaches a level: its comparisons start decided).
+struct LevelBits {
+  uint32_t pw, qw;
+};
+
+__device__ __forceinline__ LevelBits level_bits(const Accept &acc) {
+  LevelBits b;
+  b.pw = (uint32_t)(acc.P << (32 - acc.k));
+  b.qw = (uint32_t)(acc.Q << (32 - acc.k));
+  return b;
+}
+
+// Level m of the group's random words rb applied to the comparisons of all
+// 128 sites with both thresholds.
+__device__ __forceinline__ void cmp_level(const u32x4 &rb, const LevelBits &tb, int m,
+                                          uint32_t lp[4], uint32_t ep[4], uint32_t lq[4],
+                                          uint32_t eq[4]) {
+  const uint32_t pb = (tb.pw >> (31 - m)) & 1u, qb = (tb.qw >> (31 - m)) & 1u;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    lt_step(rb.v[j], pb, lp[j], ep[j]);
+    lt_step(rb.v[j], qb, lq[j], eq[j]);
+  }
+}
+
+__device__ __forceinline__ uint32_t rotl1(uint32_t x) { return __funnelshift_l(x, x, 1); }
+__device__ __forceinline__ uint32_t rotr1(uint32_t x) { return __funnelshift_r(x, x, 1); }
+
+__device__ __forceinline__ uint32_t open_candidates(const uint32_t ep[4], const uint32_t eq[4],
+                                                   const uint32_t mn[4], const uint32_t mx[4]) {
+  return ((ep[0] & mn[0]) | (eq[0] & mx[0])) | ((ep[1] & mn[1]) | (eq[1] & mx[1])) |
+         ((ep[2] & mn[2]) | (eq[2] & mx[2])) | ((ep[3] & mn[3]) | (eq[3] & mx[3]));
+}
+
+// Minima and maxima of half-sweep SP among the group's 4 words c (row y,
+// words w0 .. w0+3), from the rows below and above and the words either side.
+template <int SP>
+__device__ __forceinline__ void group_extrema(const uint32_t *B, int L, int W, uint32_t y,
+                                              uint32_t w0, const uint32_t c[4], uint32_t mn[4],
+                                              uint32_t mx[4]) {
   const uint32_t yd = (y == 0) ? L - 1 : y - 1, yu = (y == (uint32_t)L - 1) ? 0 : y + 1;
-  uint32_t *row = B + (size_t)y * W;
-  const uint4 cv = *(const uint4 *)(row + w0);
+  const uint32_t *row = B + (size_t)y * W;
   const uint4 dv = *(const uint4 *)(B + (size_t)yd * W + w0);
   const uint4 uv = *(const uint4 *)(B + (size_t)yu * W + w0);
   const uint32_t lw = row[w0 == 0 ? W - 1 : w0 - 1];
   const uint32_t rw = row[w0 + 4 == (uint32_t)W ? 0 : w0 + 4];
-  const uint32_t c[4] = {cv.x, cv.y, cv.z, cv.w};
   const uint32_t d[4] = {dv.x, dv.y, dv.z, dv.w};
   const uint32_t u[4] = {uv.x, uv.y, uv.z, uv.w};
-  const uint32_t a = active_mask(y, s);
-  // a minimum of half-sweep s has all four neighbours equal to its own bit
-  // xor s: "both equal" (table 0x81) for s = 0, "both differ" (0x42) for
-  // s = 1, on (l, r, c) and (d, u, c); a maximum the reverse
+  const uint32_t a = active_mask(y, SP);
+  // a minimum of half-sweep SP has all four neighbours equal to its own bit
+  // xor SP: "both equal" (table 0x81) for SP = 0, "both differ" (0x42) for
+  // SP = 1, on (l, r, c) and (d, u, c); a maximum the reverse
   constexpr uint32_t kMin = SP ? 0x42u : 0x81u;
   constexpr uint32_t kMax = SP ? 0x81u : 0x42u;
-  uint32_t mn[4], mx[4];
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     const uint32_t l = __funnelshift_l(j == 0 ? lw : c[j - 1], c[j], 1);
@@ -187,58 +259,167 @@ __device__ __forceinline__ void row_group_update(uint32_t *B, int L, int W, uint
     mn[j] = lop3<0x80>(lop3<kMin>(l, r, c[j]), lop3<kMin>(d[j], u[j], c[j]), a);
     mx[j] = lop3<0x80>(lop3<kMax>(l, r, c[j]), lop3<kMax>(d[j], u[j], c[j]), a);
   }
+}
+
+__device__ __forceinline__ void load_group(const uint32_t *B, int W, uint32_t y, uint32_t w0,
+                                           uint32_t c[4]) {
+  const uint4 v = *(const uint4 *)(B + (size_t)y * W + w0);
+  c[0] = v.x;
+  c[1] = v.y;
+  c[2] = v.z;
+  c[3] = v.w;
+}
+
+// First half-sweep of group g at (y, w0). Levels are drawn while any lane of
+// `lanes` has an undecided candidate (the warp runs to its last one anyway),
+// LV levels per test (a level drawn beyond the last undecided candidate
+// changes nothing decided). Out: the group's words after the moves in c; the
+// second-half state packed in LT, EQ -- word j holds the P comparison at the
+// second-half positions and the Q comparison rotated left by one bit into the
+// first-half positions -- and the next level in m.
+template <int LV>
+__device__ __forceinline__ void band_first_half(uint32_t *B, int L, int W, uint32_t y,
+                                                uint32_t w0, uint32_t g, uint32_t t,
+                                                const uint32_t *rks, const Accept &acc,
+                                                unsigned lanes, int &dH0, uint32_t c[4],
+                                                uint32_t LT[4], uint32_t EQ[4], int &m) {
+  load_group(B, W, y, w0, c);
+  uint32_t mn[4], mx[4];
+  group_extrema<0>(B, L, W, y, w0, c, mn, mx);
+  const uint64_t full = 1ull << acc.k;
+  const uint32_t lp0 = (acc.P >= full) ? ~0u : 0u, ep0 = (acc.P >= full || acc.P == 0) ? 0u : ~0u;
+  const uint32_t lq0 = (acc.Q >= full) ? ~0u : 0u, eq0 = (acc.Q >= full || acc.Q == 0) ? 0u : ~0u;
+  uint32_t lp[4], ep[4], lq[4], eq[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    lp[j] = lp0;
+    ep[j] = ep0;
+    lq[j] = lq0;
+    eq[j] = eq0;
+  }
+  const LevelPhilox ph = level_philox_init(g, t, rks);
+  const LevelBits tb = level_bits(acc);
+  m = 0;
+  while (m < acc.k) {
+    if (!__any_sync(lanes, open_candidates(ep, eq, mn, mx) != 0u)) break;
+    cmp_level(level_philox(ph, (uint32_t)m, rks), tb, m, lp, ep, lq, eq);
+    if (++m < acc.k && LV == 2) {
+      cmp_level(level_philox(ph, (uint32_t)m, rks), tb, m, lp, ep, lq, eq);
+      ++m;
+    }
+  }
   uint32_t f[4];
-  accept4<CACHE>(mn, mx, g, t, rks, acc, f, cw, cvalid, cbit);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) f[j] = (lp[j] & mn[j]) | (lq[j] & mx[j]);
   if ((f[0] | f[1] | f[2] | f[3]) != 0u)
-    *(uint4 *)(row + w0) = make_uint4(c[0] ^ f[0], c[1] ^ f[1], c[2] ^ f[2], c[3] ^ f[3]);
+    *(uint4 *)(B + (size_t)y * W + w0) =
+        make_uint4(c[0] ^ f[0], c[1] ^ f[1], c[2] ^ f[2], c[3] ^ f[3]);
+  if (g == 0 && (f[0] & 1u)) dH0 += (mn[0] & 1u) ? 2 : -2;  // site (0,0)
+  const uint32_t a0 = active_mask(y, 0);  // first-half positions
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    c[j] ^= f[j];
+    LT[j] = (lp[j] & ~a0) | (rotl1(lq[j]) & a0);
+    EQ[j] = (ep[j] & ~a0) | (rotl1(eq[j]) & a0);
+  }
+}
+
+// Second half-sweep of group g at (y, w0), its words c as the first half left
+// them, from the packed state (LT, EQ, m) that half left.
+__device__ __forceinline__ void band_second_half(uint32_t *B, int L, int W, uint32_t y,
+                                                 uint32_t w0, uint32_t g, uint32_t t,
+                                                 const uint32_t *rks, const Accept &acc,
+                                                 int &dH0, const uint32_t c[4],
+                                                 const uint32_t LT[4], const uint32_t EQ[4],
+                                                 int m) {
+  uint32_t mn[4], mx[4];
+  group_extrema<1>(B, L, W, y, w0, c, mn, mx);
+  uint32_t lp[4], ep[4], lq[4], eq[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {  // only the second-half positions are read below
+    lp[j] = LT[j];
+    ep[j] = EQ[j];
+    lq[j] = rotr1(LT[j]);
+    eq[j] = rotr1(EQ[j]);
+  }
+  if (m < acc.k && open_candidates(ep, eq, mn, mx) != 0u) {  // rare
+    const LevelPhilox ph = level_philox_init(g, t, rks);
+    const LevelBits tb = level_bits(acc);
+    for (; m < acc.k && open_candidates(ep, eq, mn, mx) != 0u; ++m)
+      cmp_level(level_philox(ph, (uint32_t)m, rks), tb, m, lp, ep, lq, eq);
+  }
+  uint32_t f[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) f[j] = (lp[j] & mn[j]) | (lq[j] & mx[j]);
+  if ((f[0] | f[1] | f[2] | f[3]) != 0u)
+    *(uint4 *)(B + (size_t)y * W + w0) =
+        make_uint4(c[0] ^ f[0], c[1] ^ f[1], c[2] ^ f[2], c[3] ^ f[3]);
   if (g == 0 && (f[0] & 1u)) dH0 += (mn[0] & 1u) ? 2 : -2;  // site (0,0)
 }
 
-// `n` sweeps of one lattice by the whole CTA.
-__device__ __forceinline__ void cta_sweeps(uint32_t *B, int L, uint32_t t0, int n,
-                                           const uint32_t *rks, const Accept &acc, int &dH0) {
+// `n` sweeps of one lattice (L % 128 == 0) by the whole CTA in band steps of
+// R = blockDim.x / (L/128) rows (all rows for small L), thread (ry, col)
+// taking group col of row y0 + ry. Thread 0 takes group 0 of row 0 in both
+// halves, so it alone sees site (0,0).
+template <int LV>
+__device__ __forceinline__ void cta_sweeps_band(uint32_t *B, int L, uint32_t t0, int n,
+                                                const uint32_t *rks, const Accept &acc, int &dH0,
+                                                BandCarry &bc) {
   const int W = L >> 5;
-  const uint32_t groups = (uint32_t)L * (uint32_t)W / 4;
-  if ((L & 127) == 0) {  // groups never straddle rows
-    const uint32_t gpr = (uint32_t)W / 4;
-    const bool pow2 = (gpr & (gpr - 1)) == 0;
-    const int lg = __ffs(gpr) - 1;
-    // a thread takes the same groups in both half-sweeps; with at most
-    // kCacheGroups of them it keeps their level-0 words between the two
-    // (with k >= 3 the later levels dominate and the local-memory round trip
-    // does not pay: -1.5 % on a k = 32 mix, +6 % at k = 1)
-    const bool cache = acc.k <= 2 && groups <= kCacheGroups * blockDim.x;
-    uint32_t cw[4 * kCacheGroups];
-    for (int i = 0; i < n; ++i) {
-      const uint32_t t = t0 + (uint32_t)i;
-      uint32_t cvalid = 0;
-      if (cache && pow2) {
-        uint32_t q = 0;
-        for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x, ++q)
-          row_group_update<true, 0, 1>(B, L, W, gpr, lg, g, t, rks, acc, dH0, cw + 4 * q, cvalid,
-                                       1u << q);
-        __syncthreads();
-        q = 0;
-        for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x, ++q)
-          row_group_update<true, 1, 2>(B, L, W, gpr, lg, g, t, rks, acc, dH0, cw + 4 * q, cvalid,
-                                       1u << q);
-      } else if (pow2) {
-        for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x)
-          row_group_update<true, 0, 0>(B, L, W, gpr, lg, g, t, rks, acc, dH0, cw, cvalid, 0u);
-        __syncthreads();
-        for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x)
-          row_group_update<true, 1, 0>(B, L, W, gpr, lg, g, t, rks, acc, dH0, cw, cvalid, 0u);
-      } else {
-        for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x)
-          row_group_update<false, 0, 0>(B, L, W, gpr, lg, g, t, rks, acc, dH0, cw, cvalid, 0u);
-        __syncthreads();
-        for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x)
-          row_group_update<false, 1, 0>(B, L, W, gpr, lg, g, t, rks, acc, dH0, cw, cvalid, 0u);
+  const uint32_t G = (uint32_t)W >> 2;
+  const uint32_t tid = threadIdx.x;
+  const uint32_t R = min(blockDim.x / G, (uint32_t)L);
+  const uint32_t nb = ((uint32_t)L + R - 1) / R;
+  const uint32_t ry = tid / G, col = tid - ry * G, w0 = 4 * col;
+  for (int i = 0; i < n; ++i) {
+    const uint32_t t = t0 + (uint32_t)i;
+    for (uint32_t j = 0; j < nb; ++j) {
+      const uint32_t y0 = j * R, rc = min(R, (uint32_t)L - y0), y = y0 + ry;
+      const bool mine = ry < rc;
+      const unsigned lanes = __ballot_sync(0xFFFFFFFFu, mine);
+      uint32_t c[4], LT[4], EQ[4];
+      int m = 0;
+      if (mine) {
+        band_first_half<LV>(B, L, W, y, w0, y * G + col, t, rks, acc, lanes, dH0, c, LT, EQ,
+                            m);
+        if (ry + 1 == rc) carry_put(bc, (int)(j & 1), col, LT, EQ, m);
+        if (y == 0) carry_put(bc, 2, col, LT, EQ, m);
+      }
+      __syncthreads();
+      if (mine && ry + 1 < rc && y != 0) {
+        band_second_half(B, L, W, y, w0, y * G + col, t, rks, acc, dH0, c, LT, EQ, m);
+      } else if (mine && ry + 1 == rc && j > 0 && y0 - 1 != 0) {
+        const uint32_t yp = y0 - 1;  // the previous band's last row
+        carry_get(bc, (int)((j - 1) & 1), col, LT, EQ, m);
+        load_group(B, W, yp, w0, c);
+        band_second_half(B, L, W, yp, w0, yp * G + col, t, rks, acc, dH0, c, LT, EQ, m);
       }
       __syncthreads();
     }
+    if (tid < 2 * G) {  // row 0 (threads 0 .. G-1) and row L-1, held back to here
+      const bool r0 = tid < G;
+      const uint32_t cl = r0 ? tid : tid - G, yy = r0 ? 0u : (uint32_t)L - 1;
+      uint32_t c[4], LT[4], EQ[4];
+      int m = 0;
+      carry_get(bc, r0 ? 2 : (int)((nb - 1) & 1), cl, LT, EQ, m);
+      load_group(B, W, yy, 4 * cl, c);
+      band_second_half(B, L, W, yy, 4 * cl, yy * G + cl, t, rks, acc, dH0, c, LT, EQ, m);
+    }
+    __syncthreads();
+  }
+}
+
+// `n` sweeps of one lattice by the whole CTA.
+template <int LV>
+__device__ __forceinline__ void cta_sweeps(uint32_t *B, int L, uint32_t t0, int n,
+                                           const uint32_t *rks, const Accept &acc, int &dH0,
+                                           BandCarry &bc) {
+  if ((L & 127) == 0) {  // groups never straddle rows
+    cta_sweeps_band<LV>(B, L, t0, n, rks, acc, dH0, bc);
     return;
   }
+  const int W = L >> 5;
+  const uint32_t groups = (uint32_t)L * (uint32_t)W / 4;
   for (int i = 0; i < n; ++i) {  // L = 32, 64, 96: groups span rows
     const uint32_t t = t0 + (uint32_t)i;
     for (int s = 0; s < 2; ++s) {
@@ -251,13 +432,21 @@ __device__ __forceinline__ void cta_sweeps(uint32_t *B, int L, uint32_t t0, int 
 
 }  // namespace
 
-__global__ void __launch_bounds__(1024, 1)
+template <int MAXT, int MINB>
+constexpr int kLevelsPerTest = (65536 / (MAXT * MINB) >= 128) ? 2 : 1;
+
+// CTAs of MAXT threads, MINB of them per SM: 1024 x 1 and 512 x 2 leave 64
+// registers a thread (one random level per candidate test), 256 x 2 leave
+// 128 (two). Several CTAs per SM fill one another's barrier waits.
+template <int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB)
 batch_sweep_kernel(uint32_t *__restrict__ arena, SlotDesc *__restrict__ slots,
                    const WorkTable *__restrict__ work, unsigned int *__restrict__ head,
                    uint32_t smem_words) {
   extern __shared__ __align__(16) uint32_t sm[];
   __shared__ int item;
   __shared__ __align__(8) uint32_t rks[20];  // round keys of the current slot's seed
+  __shared__ BandCarry carry;
   const int nwork = work->count;
   while (true) {
     if (threadIdx.x == 0) item = (int)atomicAdd(head, 1u);
@@ -283,11 +472,11 @@ batch_sweep_kernel(uint32_t *__restrict__ arena, SlotDesc *__restrict__ slots,
     if (words <= smem_words) {
       for (uint32_t w = threadIdx.x; w < words; w += blockDim.x) sm[w] = g[w];
       __syncthreads();
-      cta_sweeps(sm, d.L, d.t, n, rks, acc, dH0);
+      cta_sweeps<kLevelsPerTest<MAXT, MINB>>(sm, d.L, d.t, n, rks, acc, dH0, carry);
       for (uint32_t w = threadIdx.x; w < words; w += blockDim.x) g[w] = sm[w];
     } else {
       __syncthreads();
-      cta_sweeps(g, d.L, d.t, n, rks, acc, dH0);
+      cta_sweeps<kLevelsPerTest<MAXT, MINB>>(g, d.L, d.t, n, rks, acc, dH0, carry);
     }
     if (threadIdx.x == 0) {  // thread 0 owns group 0, the only group with site (0,0)
       slots[slot].t = d.t + (uint32_t)n;
@@ -381,8 +570,13 @@ cudaError_t launch_batch_sweeps(uint32_t *arena, SlotDesc *slots, const WorkTabl
   // the dynamic shared-memory limit was raised by batch_occupancy() before
   cudaError_t e = cudaMemsetAsync(head, 0, sizeof(unsigned int), st);
   if (e != cudaSuccess) return e;
-  batch_sweep_kernel<<<grid, threads, smem_bytes, st>>>(arena, slots, work, head,
-                                                       (uint32_t)(smem_bytes / 4));
+  const uint32_t words = (uint32_t)(smem_bytes / 4);
+  if (threads > 512)
+    batch_sweep_kernel<1024, 1><<<grid, threads, smem_bytes, st>>>(arena, slots, work, head, words);
+  else if (threads > 256)
+    batch_sweep_kernel<512, 2><<<grid, threads, smem_bytes, st>>>(arena, slots, work, head, words);
+  else
+    batch_sweep_kernel<256, 2><<<grid, threads, smem_bytes, st>>>(arena, slots, work, head, words);
   return cudaGetLastError();
 }
 
@@ -401,11 +595,13 @@ cudaError_t launch_batch_moments(const uint32_t *arena, SlotDesc *slots, const W
 
 int batch_occupancy(int threads, size_t smem_bytes) {
   int per_sm = 0;
+  const void *fn = threads > 512   ? (const void *)batch_sweep_kernel<1024, 1>
+                   : threads > 256 ? (const void *)batch_sweep_kernel<512, 2>
+                                   : (const void *)batch_sweep_kernel<256, 2>;
   // one limit for every batch: the largest staging buffer a tiling may ask for
-  cudaFuncSetAttribute((const void *)batch_sweep_kernel,
-                       cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)batch_sweep_kernel,
-                                                    threads, smem_bytes) != cudaSuccess)
+  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem_bytes) !=
+      cudaSuccess)
     return 0;
   return per_sm;
 }
