@@ -278,14 +278,16 @@ def run_gpu(args, world, rank, local):
     L = args.L
     N = L * L
     stream = torch.cuda.Stream(device=dev)
-    # the tiling (words per thread x sweeps per pass) by the library's autotuner,
-    # unless given on the command line; every choice gives the same lattice
+    # the tiling (words per thread x sweeps per pass x band rows) by the
+    # library's autotuner, unless given on the command line; every choice gives
+    # the same lattice
     tuned = None
     if args.wpt == 0 and args.fuse == 0:
-        w, f, ms = okz.okz_tune_stream(L, 1.0, 0.0, kernel=KERNELS[args.kernel], probe_sweeps=8)
-        tuned = {"words_per_thread": w, "sweeps_per_pass": f, "ms_per_sweep": ms,
-                 "candidates": "words per thread {4, 8, 16} x sweeps per pass {1, 2}, "
-                               "8 timed sweeps each (okz_tune_stream)"}
+        w, f, b, ms = okz.okz_tune_stream(L, 1.0, 0.0, kernel=KERNELS[args.kernel],
+                                          probe_sweeps=8)
+        tuned = {"words_per_thread": w, "sweeps_per_pass": f, "band_rows": b, "ms_per_sweep": ms,
+                 "candidates": "words per thread {4, 8, 16} x sweeps per pass {1, 2} x band "
+                               "rows {auto, 16, 32}, 8 timed sweeps each (okz_tune_stream)"}
     with torch.cuda.stream(stream):
         sim = okz.Simulation(L, 1.0, 0.0, seed=SEED + rank, torch_buffer=True,
                              kernel=KERNELS[args.kernel], words_per_thread=args.wpt,

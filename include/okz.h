@@ -100,6 +100,12 @@ typedef struct okz_params {
     int32_t words_per_thread; /* STREAM: 4, 8 (or 16, parity plane) words of 32 sites
                                  per thread; 0 = auto                                */
     int32_t sweeps_per_pass;  /* STREAM: 1 or 2 sweeps fused per launch; 0 = auto      */
+    int32_t band_rows;        /* STREAM: rows per CTA band, at least 4F + 4 (F the
+                                 sweeps per pass) and at most L; 0 = auto: as many
+                                 bands as the GPU holds at once, each at least
+                                 4F + 4 rows. A band streams 4F rows beyond its
+                                 own, so smaller bands trade work for parallelism.
+                                 Results do not depend on it.                      */
 } okz_params;
 
 typedef struct okz_info {
@@ -115,6 +121,7 @@ typedef struct okz_info {
     int32_t graph_chunk;       /* in-place kernels: sweeps per replay of the
                                   simulation's CUDA graph (0 = not built)       */
     uint64_t graph_replays;    /* replays of that graph so far                  */
+    int32_t band_rows;         /* stream kernels: the band_rows in use (0 = auto) */
 } okz_info;
 
 typedef struct okz_sim okz_sim;
@@ -257,20 +264,20 @@ okz_status okz_restore(okz_sim *sim, const uint32_t *planes, int in_is_device,
 
 /* okz_tune_stream -- the paper has no counterpart to this entry point (the
  * tiling of the update is this build's). Autotuner of the stream kernels'
- * launch shape for one workload: for every valid words_per_thread (4, 8, 16)
- * and sweeps_per_pass (1, 2) it creates a scratch simulation of prm (kernel
- * STREAM or PARITY_STREAM; AUTO means PARITY_STREAM), runs 4 sweeps, then
- * times probe_sweeps (>= 2) sweeps with CUDA events, and keeps the fastest
- * per sweep. The choice is remembered for (device, L, kernel, acceptance
- * mode: k = 1 with minima only, other k <= 1, k >= 2) and used by every later
- * okz_create / okz_create_ex that leaves both words_per_thread and
- * sweeps_per_pass automatic (0). Results are bit-identical for every tiling,
- * so tuning never changes a result. Writes the choice and its time per sweep
- * (any output may be NULL). Synchronizing; each scratch simulation holds
+ * launch shape for one workload: for every valid words_per_thread (4, 8, 16),
+ * sweeps_per_pass (1, 2) and band_rows (0 = auto, 16, 32) it creates a
+ * scratch simulation of prm (kernel STREAM or PARITY_STREAM; AUTO means
+ * PARITY_STREAM), runs 4 sweeps, then times probe_sweeps (>= 2) sweeps with
+ * CUDA events, and keeps the fastest per sweep. The choice is remembered for
+ * (device, L, kernel, acceptance mode: k = 1 with minima only, other k <= 1,
+ * k >= 2) and used by every later okz_create / okz_create_ex that leaves
+ * words_per_thread, sweeps_per_pass and band_rows automatic (0). Results are
+ * bit-identical for every tiling, so tuning never changes a result. Writes
+ * the choice and its time per sweep (any output may be NULL). Synchronizing; each scratch simulation holds
  * okz_device_bytes(L) for its run. Errors: EINVAL, EUNSUPPORTED (L outside the
  * stream kernels' range), ENOMEM, ECUDA, ETIMEOUT. */
 okz_status okz_tune_stream(const okz_params *prm, int32_t probe_sweeps, int32_t *wpt_out,
-                           int32_t *fuse_out, double *ms_per_sweep);
+                           int32_t *fuse_out, int32_t *band_out, double *ms_per_sweep);
 
 /* Fills *info. Synchronizing (H0 lives on the device). */
 okz_status okz_get_info(okz_sim *sim, okz_info *info);

@@ -41,7 +41,8 @@ class okz_params(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int64), ("p", ctypes.c_double), ("q", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("s_sel", ctypes.c_double),
                 ("k_max", ctypes.c_int32), ("kernel", ctypes.c_int32),
-                ("words_per_thread", ctypes.c_int32), ("sweeps_per_pass", ctypes.c_int32)]
+                ("words_per_thread", ctypes.c_int32), ("sweeps_per_pass", ctypes.c_int32),
+                ("band_rows", ctypes.c_int32)]
 
 
 class okz_info(ctypes.Structure):
@@ -49,7 +50,8 @@ class okz_info(ctypes.Structure):
                 ("k", ctypes.c_int32), ("kernel", ctypes.c_int32), ("P", ctypes.c_uint64),
                 ("Q", ctypes.c_uint64), ("device_bytes", ctypes.c_size_t),
                 ("words_per_thread", ctypes.c_int32), ("sweeps_per_pass", ctypes.c_int32),
-                ("graph_chunk", ctypes.c_int32), ("graph_replays", ctypes.c_uint64)]
+                ("graph_chunk", ctypes.c_int32), ("graph_replays", ctypes.c_uint64),
+                ("band_rows", ctypes.c_int32)]
 
 
 # C signatures: name -> (restype, argtypes)
@@ -75,7 +77,8 @@ _SIGS = {
     "okz_alu_peak": (_c.c_int, [_vp, _c.c_int32, _c.POINTER(_c.c_double),
                                 _c.POINTER(_c.c_double)]),
     "okz_tune_stream": (_c.c_int, [_c.POINTER(okz_params), _c.c_int32, _c.POINTER(_c.c_int32),
-                                   _c.POINTER(_c.c_int32), _c.POINTER(_c.c_double)]),
+                                   _c.POINTER(_c.c_int32), _c.POINTER(_c.c_int32),
+                                   _c.POINTER(_c.c_double)]),
     "okz_moments_fetch": (_c.c_int, [_vp, _c.POINTER(okz_i128), _c.POINTER(_c.c_double),
                                _c.POINTER(_c.c_double), _c.POINTER(_c.c_double)]),
     "okz_psd": (_c.c_int, [_vp, _vp]),
@@ -144,12 +147,13 @@ def okz_last_error():
 
 
 def okz_params_init(L=0, p=1.0, q=0.0, seed=0, s_sel=0.5, k_max=32, kernel=OKZ_KERNEL_AUTO,
-                    words_per_thread=0, sweeps_per_pass=0):
+                    words_per_thread=0, sweeps_per_pass=0, band_rows=0):
     prm = okz_params()
     lib().okz_params_init(ctypes.byref(prm))
     prm.L, prm.p, prm.q, prm.seed = int(L), float(p), float(q), int(seed)
     prm.s_sel, prm.k_max, prm.kernel = float(s_sel), int(k_max), int(kernel)
     prm.words_per_thread, prm.sweeps_per_pass = int(words_per_thread), int(sweeps_per_pass)
+    prm.band_rows = int(band_rows)
     return prm
 
 
@@ -209,17 +213,18 @@ def okz_alu_peak(stream=None, iters=20000):
 
 
 def okz_tune_stream(L, p, q, s_sel=0.5, k_max=32, kernel=0, probe_sweeps=8):
-    """Autotunes the stream kernels' (words per thread, sweeps per pass) for
-    this workload; later Simulations with automatic tiling use the choice.
-    -> (words_per_thread, sweeps_per_pass, ms per sweep)."""
+    """Autotunes the stream kernels' (words per thread, sweeps per pass, band
+    rows) for this workload; later Simulations with automatic tiling use the
+    choice. -> (words_per_thread, sweeps_per_pass, band_rows, ms per sweep)."""
     prm = okz_params()
     lib().okz_params_init(ctypes.byref(prm))
     prm.L, prm.p, prm.q, prm.s_sel, prm.k_max, prm.kernel = int(L), float(p), float(q), \
         float(s_sel), int(k_max), int(kernel)
-    w, f, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+    w, f, b, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
     _check(lib().okz_tune_stream(ctypes.byref(prm), int(probe_sweeps), ctypes.byref(w),
-                                 ctypes.byref(f), ctypes.byref(ms)), "okz_tune_stream")
-    return w.value, f.value, ms.value
+                                 ctypes.byref(f), ctypes.byref(b), ctypes.byref(ms)),
+           "okz_tune_stream")
+    return w.value, f.value, b.value, ms.value
 
 
 def okz_moments_enqueue(h):
@@ -335,11 +340,11 @@ class Simulation:
 
     def __init__(self, L, p=1.0, q=0.0, seed=0, s_sel=0.5, k_max=32,
                  kernel=OKZ_KERNEL_AUTO, torch_buffer=False, stream=None,
-                 words_per_thread=0, sweeps_per_pass=0):
+                 words_per_thread=0, sweeps_per_pass=0, band_rows=0):
         self.L = int(L)
         self._buf = None
         prm = okz_params_init(L, p, q, seed, s_sel, k_max, kernel, words_per_thread,
-                              sweeps_per_pass)
+                              sweeps_per_pass, band_rows)
         if torch_buffer:
             import torch
             nbytes = okz_device_bytes(L)
@@ -395,6 +400,10 @@ class Simulation:
     @property
     def fuse(self):
         return self.info().sweeps_per_pass
+
+    @property
+    def band_rows(self):
+        return self.info().band_rows
 
     def synchronize(self):
         okz_synchronize(self.h)

@@ -20,6 +20,7 @@ struct okz_sim {
   bool parity;  // device state is one height-parity plane (else two slope planes)
   int wpt;   // stream kernel: words per thread
   int fuse;  // stream kernel: sweeps per launch
+  int band_rows;  // stream kernel: rows per CTA band (0 = auto)
   int device;
   cudaStream_t stream;
   bool own_stream;
@@ -145,9 +146,12 @@ struct TuneKey {
   }
 };
 static std::mutex g_tune_mu;
-static std::map<TuneKey, std::pair<int, int>> g_tuned;
+struct Tiling {
+  int wpt, fuse, band_rows;
+};
+static std::map<TuneKey, Tiling> g_tuned;
 
-static bool tuned_tiling(int64_t L, int kernel, int mode, int *wpt, int *fuse) {
+static bool tuned_tiling(int64_t L, int kernel, int mode, int *wpt, int *fuse, int *band_rows) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
     cudaGetLastError();
@@ -156,8 +160,9 @@ static bool tuned_tiling(int64_t L, int kernel, int mode, int *wpt, int *fuse) {
   std::lock_guard<std::mutex> lock(g_tune_mu);
   auto it = g_tuned.find(TuneKey{dev, L, kernel, mode});
   if (it == g_tuned.end()) return false;
-  *wpt = it->second.first;
-  *fuse = it->second.second;
+  *wpt = it->second.wpt;
+  *fuse = it->second.fuse;
+  *band_rows = it->second.band_rows;
   return true;
 }
 
@@ -187,6 +192,7 @@ void okz_params_init(okz_params *prm) {
   prm->kernel = OKZ_KERNEL_AUTO;
   prm->words_per_thread = 0;
   prm->sweeps_per_pass = 0;
+  prm->band_rows = 0;
 }
 
 okz_status okz_thresholds(double p, double q, double s_sel, int32_t k_max, int32_t *k,
@@ -253,12 +259,13 @@ okz_status okz_create_ex(const okz_params *prm, void *dev_buf, size_t bytes, voi
     set_error("the streaming kernels need L % 4096 == 0 and L <= 131072");
     return OKZ_EUNSUPPORTED;
   }
-  int wpt = prm->words_per_thread, fuse = prm->sweeps_per_pass;
-  if (streamed && wpt == 0 && fuse == 0) {  // a tiling okz_tune_stream measured best
-    int tw = 0, tf = 0;
-    if (tuned_tiling(prm->L, kernel, stream_mode(k, P, Q), &tw, &tf)) {
+  int wpt = prm->words_per_thread, fuse = prm->sweeps_per_pass, band = prm->band_rows;
+  if (streamed && wpt == 0 && fuse == 0 && band == 0) {  // okz_tune_stream's best tiling
+    int tw = 0, tf = 0, tb = 0;
+    if (tuned_tiling(prm->L, kernel, stream_mode(k, P, Q), &tw, &tf, &tb)) {
       wpt = tw;
       fuse = tf;
+      band = tb;
     }
   }
   if (streamed) {
@@ -294,9 +301,14 @@ okz_status okz_create_ex(const okz_params *prm, void *dev_buf, size_t bytes, voi
                 "stream kernel also takes 16 with L % 16384 == 0) and sweeps_per_pass 1 or 2");
       return OKZ_EINVAL;
     }
+    if (band != 0 && (band < stream_min_band(fuse) || band > prm->L)) {
+      set_error("band_rows must be 0 (auto) or lie in [4F + 4, L], F the sweeps per pass");
+      return OKZ_EINVAL;
+    }
   } else {
     wpt = 0;
     fuse = 1;
+    band = 0;
   }
   const Layout lay = layout_for(prm->L);
   if (dev_buf && (bytes < lay.total || ((uintptr_t)dev_buf & 255u))) {
@@ -317,6 +329,7 @@ okz_status okz_create_ex(const okz_params *prm, void *dev_buf, size_t bytes, voi
   sim->parity = kernel == OKZ_KERNEL_PARITY_PLAIN || kernel == OKZ_KERNEL_PARITY_STREAM;
   sim->wpt = wpt;
   sim->fuse = fuse;
+  sim->band_rows = band;
   sim->lay = lay;
   sim->t = 0;
   sim->cur = 0;
@@ -479,12 +492,12 @@ okz_status okz_sweep(okz_sim *sim, int64_t n) {
       step = (sim->fuse == 2 && n - done >= 2) ? 2 : 1;
       if (sim->parity)
         e = launch_parity_stream(sim->planes[sim->cur], sim->planes[1 - sim->cur], L, t,
-                                 sim->prm.seed, sim->acc, sim->wpt, (int)step, sim->ctrl,
-                                 sim->stream);
+                                 sim->prm.seed, sim->acc, sim->wpt, (int)step,
+                                 sim->band_rows, sim->ctrl, sim->stream);
       else
         e = launch_sweep_stream(sim->planes[sim->cur], sim->planes[1 - sim->cur], L, t,
-                                sim->prm.seed, sim->acc, sim->wpt, (int)step, sim->ctrl,
-                                sim->stream);
+                                sim->prm.seed, sim->acc, sim->wpt, (int)step, sim->band_rows,
+                                sim->ctrl, sim->stream);
       if (e == cudaSuccess) sim->cur = 1 - sim->cur;
     } else {
       e = enqueue_inplace_sweep(sim, t, sim->stream, nullptr);
@@ -840,11 +853,12 @@ okz_status okz_get_info(okz_sim *sim, okz_info *info) {
   info->device_bytes = sim->lay.total;
   info->words_per_thread = sim->wpt;
   info->sweeps_per_pass = sim->fuse;
+  info->band_rows = sim->band_rows;
   return OKZ_OK;
 }
 
 okz_status okz_tune_stream(const okz_params *prm, int32_t probe_sweeps, int32_t *wpt_out,
-                           int32_t *fuse_out, double *ms_per_sweep) {
+                           int32_t *fuse_out, int32_t *band_out, double *ms_per_sweep) {
   if (!prm || probe_sweeps < 2) {
     set_error("okz_tune_stream: null parameters or probe_sweeps < 2");
     return OKZ_EINVAL;
@@ -866,55 +880,59 @@ okz_status okz_tune_stream(const okz_params *prm, int32_t probe_sweeps, int32_t 
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
   double best = 1e300;
-  int bw = 0, bf = 0;
-  const int wpts[3] = {4, 8, 16};
+  int bw = 0, bf = 0, bb = 0;
+  const int wpts[3] = {4, 8, 16}, bands[3] = {0, 16, 32};
   for (int wi = 0; wi < 3; ++wi)
-    for (int f = 1; f <= 2; ++f) {
-      const int w = wpts[wi];
-      const bool ok = kernel == OKZ_KERNEL_PARITY_STREAM ? parity_wpt_valid(prm->L, w)
-                                                         : stream_wpt_valid(prm->L, w);
-      if (!ok) continue;
-      okz_params q = *prm;
-      q.kernel = kernel;
-      q.words_per_thread = w;
-      q.sweeps_per_pass = f;
-      okz_sim *sim = nullptr;
-      st = okz_create_ex(&q, nullptr, 0, nullptr, &sim);
-      if (st != OKZ_OK) return st;
-      cudaEvent_t e0 = nullptr, e1 = nullptr;
-      e = cudaEventCreate(&e0);
-      if (e == cudaSuccess) e = cudaEventCreate(&e1);
-      float ms = 0.0f;
-      if (e == cudaSuccess) {
-        // past the striped start (its first sweeps move every site), then timed
-        okz_status s2 = okz_sweep(sim, 4);
-        if (s2 == OKZ_OK) e = cudaEventRecord(e0, sim->stream);
-        if (s2 == OKZ_OK && e == cudaSuccess) s2 = okz_sweep(sim, probe_sweeps);
-        if (s2 == OKZ_OK && e == cudaSuccess) e = cudaEventRecord(e1, sim->stream);
-        if (s2 == OKZ_OK && e == cudaSuccess) e = cudaEventSynchronize(e1);
-        if (s2 == OKZ_OK && e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-        if (s2 != OKZ_OK) st = s2;
+    for (int f = 1; f <= 2; ++f)
+      for (int bi = 0; bi < 3; ++bi) {
+        const int w = wpts[wi];
+        const bool ok = kernel == OKZ_KERNEL_PARITY_STREAM ? parity_wpt_valid(prm->L, w)
+                                                           : stream_wpt_valid(prm->L, w);
+        if (!ok || (bands[bi] != 0 && bands[bi] < stream_min_band(f))) continue;
+        okz_params q = *prm;
+        q.kernel = kernel;
+        q.words_per_thread = w;
+        q.sweeps_per_pass = f;
+        q.band_rows = bands[bi];
+        okz_sim *sim = nullptr;
+        st = okz_create_ex(&q, nullptr, 0, nullptr, &sim);
+        if (st != OKZ_OK) return st;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        e = cudaEventCreate(&e0);
+        if (e == cudaSuccess) e = cudaEventCreate(&e1);
+        float ms = 0.0f;
+        if (e == cudaSuccess) {
+          // past the striped start (its first sweeps move every site), then timed
+          okz_status s2 = okz_sweep(sim, 4);
+          if (s2 == OKZ_OK) e = cudaEventRecord(e0, sim->stream);
+          if (s2 == OKZ_OK && e == cudaSuccess) s2 = okz_sweep(sim, probe_sweeps);
+          if (s2 == OKZ_OK && e == cudaSuccess) e = cudaEventRecord(e1, sim->stream);
+          if (s2 == OKZ_OK && e == cudaSuccess) e = cudaEventSynchronize(e1);
+          if (s2 == OKZ_OK && e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+          if (s2 != OKZ_OK) st = s2;
+        }
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        const okz_status s3 = sync_and_check(sim);
+        okz_destroy(sim);
+        if (st != OKZ_OK) return st;
+        if (e != cudaSuccess) return cuda_fail(e, "okz_tune_stream timing");
+        if (s3 != OKZ_OK) return s3;
+        const double per = ms / probe_sweeps;
+        if (per < best) {
+          best = per;
+          bw = w;
+          bf = f;
+          bb = bands[bi];
+        }
       }
-      if (e0) cudaEventDestroy(e0);
-      if (e1) cudaEventDestroy(e1);
-      const okz_status s3 = sync_and_check(sim);
-      okz_destroy(sim);
-      if (st != OKZ_OK) return st;
-      if (e != cudaSuccess) return cuda_fail(e, "okz_tune_stream timing");
-      if (s3 != OKZ_OK) return s3;
-      const double per = ms / probe_sweeps;
-      if (per < best) {
-        best = per;
-        bw = w;
-        bf = f;
-      }
-    }
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    g_tuned[TuneKey{dev, prm->L, kernel, stream_mode(k, P, Q)}] = {bw, bf};
+    g_tuned[TuneKey{dev, prm->L, kernel, stream_mode(k, P, Q)}] = Tiling{bw, bf, bb};
   }
   if (wpt_out) *wpt_out = bw;
   if (fuse_out) *fuse_out = bf;
+  if (band_out) *band_out = bb;
   if (ms_per_sweep) *ms_per_sweep = best;
   return OKZ_OK;
 }

@@ -40,7 +40,8 @@ bool stream_wpt_valid(int64_t L, int wpt);
 // Runs `fuse` (1 or 2) sweeps t, t+1, .. in one pass from src to dst.
 cudaError_t launch_sweep_stream(const uint32_t *src, uint32_t *dst, int64_t L,
                                 uint32_t t, uint64_t seed, const Accept &acc,
-                                int wpt, int fuse, Ctrl *ctrl, cudaStream_t st);
+                                int wpt, int fuse, int band_rows, Ctrl *ctrl,
+                                cudaStream_t st);
 // Measurement: column heights, then exact power sums about H0 into ctrl->sum.
 // nmom = 2 (S1, S2) or 4 (S1..S4). parity: the state is a height-parity plane.
 cudaError_t launch_power_sums(const uint32_t *planes, int64_t L, bool parity, int nmom,
@@ -58,11 +59,23 @@ cudaError_t launch_heights(const uint32_t *planes, int64_t L, bool parity, int64
 cudaError_t launch_parity_halfsweep(uint32_t *B, int64_t L, int s, uint32_t t, uint64_t seed,
                                     const Accept &acc, Ctrl *ctrl, cudaStream_t st,
                                     const unsigned int *t_base = nullptr);
+// Grid of a stream-kernel launch (both kernels): bands of band_rows rows,
+// or (band_rows = 0) as many bands as the GPU holds at once (`capacity`
+// CTAs), each at least 4F + 4 rows -- a band streams 2F rows either side of
+// its own, and the next band's stream must start above row 2F for the
+// tracking of h(0,0).
+inline int stream_grid(int L, int F, int band_rows, int capacity) {
+  int grid = band_rows > 0 ? L / band_rows : capacity;
+  if (band_rows <= 0 && grid > L / (4 * F + 4)) grid = L / (4 * F + 4);
+  return grid < 1 ? 1 : grid;
+}
+inline int stream_min_band(int F) { return 4 * F + 4; }
+
 // The parity stream kernel also takes 16 words per thread: L % 16384 == 0.
 bool parity_wpt_valid(int64_t L, int wpt);
 cudaError_t launch_parity_stream(const uint32_t *src, uint32_t *dst, int64_t L, uint32_t t,
                                  uint64_t seed, const Accept &acc, int wpt, int fuse,
-                                 Ctrl *ctrl, cudaStream_t st);
+                                 int band_rows, Ctrl *ctrl, cudaStream_t st);
 cudaError_t launch_ddrs(uint32_t *B, int64_t L, uint32_t t, uint64_t seed, uint64_t P32,
                         uint64_t Q32, Ctrl *ctrl, cudaStream_t st);
 cudaError_t launch_to_slopes(const uint32_t *B, int64_t L, uint32_t *out, cudaStream_t st);

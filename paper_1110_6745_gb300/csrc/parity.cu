@@ -381,7 +381,8 @@ parity_stream_kernel(const uint32_t *__restrict__ src, uint32_t *__restrict__ ds
         }
       }
       // H0 = h(0,0): site (0,0) moves in the s = 0 stages; only CTA 0 meets
-      // the unwrapped row 0 (CTA bands are at least 32 rows high)
+      // the unwrapped row 0 (bands are at least 4F + 4 rows high, so the
+      // next CTA's stream starts above row 2F)
       if (tid == 0) {
         const int r = r_origin + i;
 #pragma unroll
@@ -471,7 +472,7 @@ struct PPlan {
   size_t smem;
 };
 
-PPlan pplan_for(int L, int wpt, const void *fn) {
+PPlan pplan_for(int L, int wpt, int F, int band_rows, const void *fn) {
   PPlan p;
   p.threads = L / (32 * wpt);
   const size_t slot = (size_t)(L / 8);
@@ -486,22 +487,21 @@ PPlan pplan_for(int L, int wpt, const void *fn) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, p.threads, p.smem);
   if (per_sm < 1) per_sm = 1;
-  int grid = sms * per_sm;
-  if (grid > L / 32) grid = L / 32;  // at least 32 rows per band
-  if (grid < 1) grid = 1;
-  p.grid = grid;
+  p.grid = stream_grid(L, F, band_rows, sms * per_sm);
   return p;
 }
 
 template <int WPT, int F, int MODE, bool SMALL = false>
 cudaError_t plaunch(const uint32_t *src, uint32_t *dst, int L, uint32_t t, uint64_t seed,
-                    const Accept &acc, const PModes &md, Ctrl *ctrl, cudaStream_t st) {
-  static thread_local int cached_L = 0;
+                    const Accept &acc, const PModes &md, int band_rows, Ctrl *ctrl,
+                    cudaStream_t st) {
+  static thread_local int cached_L = 0, cached_band = -1;
   static thread_local PPlan plan;
   const void *fn = (const void *)parity_stream_kernel<WPT, F, MODE, SMALL>;
-  if (cached_L != L) {
-    plan = pplan_for(L, WPT, fn);
+  if (cached_L != L || cached_band != band_rows) {
+    plan = pplan_for(L, WPT, F, band_rows, fn);
     cached_L = L;
+    cached_band = band_rows;
   }
   parity_stream_kernel<WPT, F, MODE, SMALL><<<plan.grid, plan.threads, plan.smem, st>>>(
       src, dst, L, plan.stages, t, round_keys(seed), acc, md, ctrl);
@@ -510,22 +510,22 @@ cudaError_t plaunch(const uint32_t *src, uint32_t *dst, int L, uint32_t t, uint6
 
 template <int MODE>
 cudaError_t plaunch_mode(const uint32_t *src, uint32_t *dst, int L, uint32_t t, uint64_t seed,
-                         const Accept &acc, const PModes &md, int wpt, int fuse, Ctrl *ctrl,
-                         cudaStream_t st) {
+                         const Accept &acc, const PModes &md, int wpt, int fuse, int band_rows,
+                         Ctrl *ctrl, cudaStream_t st) {
   if (wpt == 16) {  // rows of at most 256 threads (parity_wpt_valid)
-    if (fuse == 2) return plaunch<16, 2, MODE, true>(src, dst, L, t, seed, acc, md, ctrl, st);
-    return plaunch<16, 1, MODE, true>(src, dst, L, t, seed, acc, md, ctrl, st);
+    if (fuse == 2) return plaunch<16, 2, MODE, true>(src, dst, L, t, seed, acc, md, band_rows, ctrl, st);
+    return plaunch<16, 1, MODE, true>(src, dst, L, t, seed, acc, md, band_rows, ctrl, st);
   }
   if (wpt == 8) {
-    if (fuse == 2) return plaunch<8, 2, MODE>(src, dst, L, t, seed, acc, md, ctrl, st);
-    return plaunch<8, 1, MODE>(src, dst, L, t, seed, acc, md, ctrl, st);
+    if (fuse == 2) return plaunch<8, 2, MODE>(src, dst, L, t, seed, acc, md, band_rows, ctrl, st);
+    return plaunch<8, 1, MODE>(src, dst, L, t, seed, acc, md, band_rows, ctrl, st);
   }
   if (L / 128 <= 256) {  // rows of at most 256 threads
-    if (fuse == 2) return plaunch<4, 2, MODE, true>(src, dst, L, t, seed, acc, md, ctrl, st);
-    return plaunch<4, 1, MODE, true>(src, dst, L, t, seed, acc, md, ctrl, st);
+    if (fuse == 2) return plaunch<4, 2, MODE, true>(src, dst, L, t, seed, acc, md, band_rows, ctrl, st);
+    return plaunch<4, 1, MODE, true>(src, dst, L, t, seed, acc, md, band_rows, ctrl, st);
   }
-  if (fuse == 2) return plaunch<4, 2, MODE>(src, dst, L, t, seed, acc, md, ctrl, st);
-  return plaunch<4, 1, MODE>(src, dst, L, t, seed, acc, md, ctrl, st);
+  if (fuse == 2) return plaunch<4, 2, MODE>(src, dst, L, t, seed, acc, md, band_rows, ctrl, st);
+  return plaunch<4, 1, MODE>(src, dst, L, t, seed, acc, md, band_rows, ctrl, st);
 }
 
 }  // namespace
@@ -538,7 +538,7 @@ bool parity_wpt_valid(int64_t L, int wpt) {
 
 cudaError_t launch_parity_stream(const uint32_t *src, uint32_t *dst, int64_t L, uint32_t t,
                                  uint64_t seed, const Accept &acc, int wpt, int fuse,
-                                 Ctrl *ctrl, cudaStream_t st) {
+                                 int band_rows, Ctrl *ctrl, cudaStream_t st) {
   PModes md{0, 0, 0, 0};
   int mode = kPModeGen;
   if (acc.k <= 1) {
@@ -553,10 +553,10 @@ cudaError_t launch_parity_stream(const uint32_t *src, uint32_t *dst, int64_t L, 
   }
   const int Li = (int)L;
   if (mode == kPModeHalf)
-    return plaunch_mode<kPModeHalf>(src, dst, Li, t, seed, acc, md, wpt, fuse, ctrl, st);
+    return plaunch_mode<kPModeHalf>(src, dst, Li, t, seed, acc, md, wpt, fuse, band_rows, ctrl, st);
   if (mode == kPModeK1)
-    return plaunch_mode<kPModeK1>(src, dst, Li, t, seed, acc, md, wpt, fuse, ctrl, st);
-  return plaunch_mode<kPModeGen>(src, dst, Li, t, seed, acc, md, wpt, fuse, ctrl, st);
+    return plaunch_mode<kPModeK1>(src, dst, Li, t, seed, acc, md, wpt, fuse, band_rows, ctrl, st);
+  return plaunch_mode<kPModeGen>(src, dst, Li, t, seed, acc, md, wpt, fuse, band_rows, ctrl, st);
 }
 
 }  // namespace okz

@@ -352,9 +352,9 @@ struct StreamPlan {
   size_t smem;
 };
 
-// Launch plan: ring depth from the shared-memory budget, grid from occupancy,
-// at least 32 rows per CTA so the 4F-row halo stays small.
-StreamPlan plan_for(int L, int wpt, const void *fn) {
+// Launch plan: ring depth from the shared-memory budget, grid from occupancy
+// and the band height (stream_grid).
+StreamPlan plan_for(int L, int wpt, int F, int band_rows, const void *fn) {
   StreamPlan p;
   p.threads = L / (32 * wpt);
   const size_t slot = (size_t)2 * (size_t)(L / 8);
@@ -370,22 +370,21 @@ StreamPlan plan_for(int L, int wpt, const void *fn) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, p.threads, p.smem);
   if (per_sm < 1) per_sm = 1;
-  int grid = sms * per_sm;
-  if (grid > L / 32) grid = L / 32;
-  if (grid < 1) grid = 1;
-  p.grid = grid;
+  p.grid = stream_grid(L, F, band_rows, sms * per_sm);
   return p;
 }
 
 template <int WPT, int F, int MODE>
 cudaError_t launch_cfg(const uint32_t *src, uint32_t *dst, int L, uint32_t t, uint64_t seed,
-                       const Accept &acc, const Modes &md, Ctrl *ctrl, cudaStream_t st) {
-  static thread_local int cached_L = 0;
+                       const Accept &acc, const Modes &md, int band_rows, Ctrl *ctrl,
+                       cudaStream_t st) {
+  static thread_local int cached_L = 0, cached_band = -1;
   static thread_local StreamPlan plan;
   const void *fn = (const void *)sweep_stream_kernel<WPT, F, MODE>;
-  if (cached_L != L) {
-    plan = plan_for(L, WPT, fn);
+  if (cached_L != L || cached_band != band_rows) {
+    plan = plan_for(L, WPT, F, band_rows, fn);
     cached_L = L;
+    cached_band = band_rows;
   }
   sweep_stream_kernel<WPT, F, MODE><<<plan.grid, plan.threads, plan.smem, st>>>(
       src, dst, L, plan.stages, t, seed, acc, md, ctrl);
@@ -394,14 +393,14 @@ cudaError_t launch_cfg(const uint32_t *src, uint32_t *dst, int L, uint32_t t, ui
 
 template <int MODE>
 cudaError_t launch_mode(const uint32_t *src, uint32_t *dst, int L, uint32_t t, uint64_t seed,
-                        const Accept &acc, const Modes &md, int wpt, int fuse, Ctrl *ctrl,
-                        cudaStream_t st) {
+                        const Accept &acc, const Modes &md, int wpt, int fuse, int band_rows,
+                        Ctrl *ctrl, cudaStream_t st) {
   if (wpt == 8) {
-    if (fuse == 2) return launch_cfg<8, 2, MODE>(src, dst, L, t, seed, acc, md, ctrl, st);
-    return launch_cfg<8, 1, MODE>(src, dst, L, t, seed, acc, md, ctrl, st);
+    if (fuse == 2) return launch_cfg<8, 2, MODE>(src, dst, L, t, seed, acc, md, band_rows, ctrl, st);
+    return launch_cfg<8, 1, MODE>(src, dst, L, t, seed, acc, md, band_rows, ctrl, st);
   }
-  if (fuse == 2) return launch_cfg<4, 2, MODE>(src, dst, L, t, seed, acc, md, ctrl, st);
-  return launch_cfg<4, 1, MODE>(src, dst, L, t, seed, acc, md, ctrl, st);
+  if (fuse == 2) return launch_cfg<4, 2, MODE>(src, dst, L, t, seed, acc, md, band_rows, ctrl, st);
+  return launch_cfg<4, 1, MODE>(src, dst, L, t, seed, acc, md, band_rows, ctrl, st);
 }
 
 }  // namespace
@@ -415,7 +414,7 @@ bool stream_wpt_valid(int64_t L, int wpt) {
 
 cudaError_t launch_sweep_stream(const uint32_t *src, uint32_t *dst, int64_t L, uint32_t t,
                                 uint64_t seed, const Accept &acc, int wpt, int fuse,
-                                Ctrl *ctrl, cudaStream_t st) {
+                                int band_rows, Ctrl *ctrl, cudaStream_t st) {
   Modes md{0, 0, 0, 0};
   int mode = kModeGen;
   if (acc.k <= 1) {
@@ -434,10 +433,10 @@ cudaError_t launch_sweep_stream(const uint32_t *src, uint32_t *dst, int64_t L, u
   }
   const int Li = (int)L;
   if (mode == kModeHalf)
-    return launch_mode<kModeHalf>(src, dst, Li, t, seed, acc, md, wpt, fuse, ctrl, st);
+    return launch_mode<kModeHalf>(src, dst, Li, t, seed, acc, md, wpt, fuse, band_rows, ctrl, st);
   if (mode == kModeK1)
-    return launch_mode<kModeK1>(src, dst, Li, t, seed, acc, md, wpt, fuse, ctrl, st);
-  return launch_mode<kModeGen>(src, dst, Li, t, seed, acc, md, wpt, fuse, ctrl, st);
+    return launch_mode<kModeK1>(src, dst, Li, t, seed, acc, md, wpt, fuse, band_rows, ctrl, st);
+  return launch_mode<kModeGen>(src, dst, Li, t, seed, acc, md, wpt, fuse, band_rows, ctrl, st);
 }
 
 }  // namespace okz

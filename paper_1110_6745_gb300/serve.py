@@ -114,7 +114,7 @@ class Server:
         for L, p, q in classes:
             if L >= self.large_threshold and (L, p, q) not in done:
                 done[(L, p, q)] = okz.okz_tune_stream(L, p, q, probe_sweeps=8)
-        return {"%d,%g,%g" % k: list(v[:2]) for k, v in done.items()}
+        return {"%d,%g,%g" % k: list(v[:3]) for k, v in done.items()}
 
     # -- admission ----------------------------------------------------------
     def _admit(self, now, small_ok):

@@ -161,12 +161,12 @@ def test_tuned_tiling_is_bit_identical(okz, orc, L, p, q, kernel):
     base = okz.Simulation(L, p, q, seed=61, kernel=kernel)
     default = (base.wpt, base.fuse)
     base.close()
-    wpt, fuse, ms = okz.okz_tune_stream(L, p, q, kernel=kernel, probe_sweeps=4)
-    assert ms > 0 and (wpt, fuse) != (0, 0)
+    wpt, fuse, band, ms = okz.okz_tune_stream(L, p, q, kernel=kernel, probe_sweeps=4)
+    assert ms > 0 and (wpt, fuse) != (0, 0) and band in (0, 16, 32)
     a = okz.Simulation(L, p, q, seed=61, kernel=kernel)
-    assert (a.wpt, a.fuse) == (wpt, fuse)
+    assert (a.wpt, a.fuse, a.band_rows) == (wpt, fuse, band)
     b = okz.Simulation(L, p, q, seed=61, kernel=kernel, words_per_thread=default[0],
-                       sweeps_per_pass=default[1])
+                       sweeps_per_pass=default[1], band_rows=32)
     a.sweep(9)
     b.sweep(9)
     pa, ha, ta = a.state()
@@ -178,6 +178,38 @@ def test_tuned_tiling_is_bit_identical(okz, orc, L, p, q, kernel):
         _compare(a, ref)
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("L,p,q", [(8192, 0.75, 0.25), (4096, 1.0, 0.0), (4096, 0.95, 0.05)])
+def test_band_heights_are_bit_identical(okz, orc, L, p, q):
+    """The stream kernels' band height (okz_params.band_rows) is a launch
+    shape only: bands of 8 and 13 rows (one sweep per pass), 12 and 32 (two)
+    and the automatic choice give the same lattice in both stream kernels,
+    and at L = 4096 the oracle's (7 sweeps: a fused pass and a single one)."""
+    n = 7
+    ref = None
+    if L == 4096:
+        ref = orc.Sim(L, p, q, 73)
+        ref.sweep(n)
+    first = None
+    for kernel, fuse, band in [(okz.OKZ_KERNEL_PARITY_STREAM, 1, 0),
+                               (okz.OKZ_KERNEL_PARITY_STREAM, 1, 8),
+                               (okz.OKZ_KERNEL_PARITY_STREAM, 1, 13),
+                               (okz.OKZ_KERNEL_PARITY_STREAM, 2, 12),
+                               (okz.OKZ_KERNEL_PARITY_STREAM, 2, 32),
+                               (okz.OKZ_KERNEL_STREAM, 1, 8),
+                               (okz.OKZ_KERNEL_STREAM, 2, 0)]:
+        with okz.Simulation(L, p, q, seed=73, kernel=kernel, words_per_thread=4,
+                            sweeps_per_pass=fuse, band_rows=band) as sim:
+            assert sim.band_rows == band
+            sim.sweep(n)
+            planes, H0, t = sim.state()
+            if first is None:
+                first = (planes, H0, t)
+            else:
+                assert np.array_equal(planes, first[0]) and (H0, t) == first[1:], (kernel, fuse, band)
+            if ref is not None:
+                _compare(sim, ref)
 
 
 def test_wpt16_rejected_where_invalid(okz):
