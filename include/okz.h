@@ -100,10 +100,10 @@ typedef struct okz_params {
     int32_t words_per_thread; /* STREAM: 4, 8 (or 16, parity plane) words of 32 sites
                                  per thread; 0 = auto                                */
     int32_t sweeps_per_pass;  /* STREAM: 1 or 2 sweeps fused per launch; 0 = auto      */
-    int32_t band_rows;        /* STREAM: rows per CTA band, at least 4F + 4 (F the
+    int32_t band_rows;        /* STREAM: rows per CTA band, at least 4F + 1 (F the
                                  sweeps per pass) and at most L; 0 = auto: as many
                                  bands as the GPU holds at once, each at least
-                                 4F + 4 rows. A band streams 4F rows beyond its
+                                 4F + 1 rows. A band streams 4F rows beyond its
                                  own, so smaller bands trade work for parallelism.
                                  Results do not depend on it.                      */
 } okz_params;

@@ -302,7 +302,7 @@ okz_status okz_create_ex(const okz_params *prm, void *dev_buf, size_t bytes, voi
       return OKZ_EINVAL;
     }
     if (band != 0 && (band < stream_min_band(fuse) || band > prm->L)) {
-      set_error("band_rows must be 0 (auto) or lie in [4F + 4, L], F the sweeps per pass");
+      set_error("band_rows must be 0 (auto) or lie in [4F + 1, L], F the sweeps per pass");
       return OKZ_EINVAL;
     }
   } else {

@@ -61,15 +61,15 @@ cudaError_t launch_parity_halfsweep(uint32_t *B, int64_t L, int s, uint32_t t, u
                                     const unsigned int *t_base = nullptr);
 // Grid of a stream-kernel launch (both kernels): bands of band_rows rows,
 // or (band_rows = 0) as many bands as the GPU holds at once (`capacity`
-// CTAs), each at least 4F + 4 rows -- a band streams 2F rows either side of
-// its own, and the next band's stream must start above row 2F for the
-// tracking of h(0,0).
+// CTAs), each at least 4F + 1 rows -- a band streams 2F rows either side of
+// its own, and only the first band's stream may meet the unwrapped rows
+// 0 .. 2F, where the tracking of h(0,0) looks.
+inline int stream_min_band(int F) { return 4 * F + 1; }
 inline int stream_grid(int L, int F, int band_rows, int capacity) {
   int grid = band_rows > 0 ? L / band_rows : capacity;
-  if (band_rows <= 0 && grid > L / (4 * F + 4)) grid = L / (4 * F + 4);
+  if (band_rows <= 0 && grid > L / stream_min_band(F)) grid = L / stream_min_band(F);
   return grid < 1 ? 1 : grid;
 }
-inline int stream_min_band(int F) { return 4 * F + 4; }
 
 // The parity stream kernel also takes 16 words per thread: L % 16384 == 0.
 bool parity_wpt_valid(int64_t L, int wpt);

@@ -381,7 +381,7 @@ parity_stream_kernel(const uint32_t *__restrict__ src, uint32_t *__restrict__ ds
         }
       }
       // H0 = h(0,0): site (0,0) moves in the s = 0 stages; only CTA 0 meets
-      // the unwrapped row 0 (bands are at least 4F + 4 rows high, so the
+      // the unwrapped row 0 (bands are at least 4F + 1 rows high, so the
       // next CTA's stream starts above row 2F)
       if (tid == 0) {
         const int r = r_origin + i;

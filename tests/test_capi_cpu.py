@@ -101,9 +101,9 @@ def test_tune_stream_rejects_bad_requests(okz):
     assert e.value.status == okz.OKZ_EUNSUPPORTED
 
 
-@pytest.mark.parametrize("fuse,band", [(1, 7), (2, 11), (1, 8193), (2, -1)])
+@pytest.mark.parametrize("fuse,band", [(1, 4), (2, 8), (1, 8193), (2, -1)])
 def test_band_rows_checked_before_touching_cuda(okz, fuse, band):
-    """A stream kernel's band is at least 4F + 4 rows (F sweeps per pass) and
+    """A stream kernel's band is at least 4F + 1 rows (F sweeps per pass) and
     at most L; 0 asks for the automatic height."""
     prm = okz.okz_params_init(L=8192, kernel=okz.OKZ_KERNEL_PARITY_STREAM, words_per_thread=4,
                               sweeps_per_pass=fuse, band_rows=band)
