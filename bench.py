@@ -55,8 +55,8 @@ N_SMS = 152
 #   ddrs_kernel           L = 32768, one launch = 1 sweep
 #   profile_count_tma_kernel  L = 65536, one profile pass
 TRAFFIC = {
-    "parity": ((556869376 + 485988608) / 65536 ** 2, "parity.cu",
-               "804ee68040f74f9233afa4baa5220f61551c75144c1729f71dd97aabe8a6d5ba"),
+    "parity": ((556844800 + 485688064) / 65536 ** 2, "parity.cu",
+               "7cb3b808cb3c3d5fabbbec85770cac2fb0b6ed80ff42eb0e57d46b543f88c4da"),
     "ddrs": ((134544640 + 73219072) / 32768 ** 2, "ddrs.cu",
              "c2f242e7e5e1b6fc82f8f918aac71218c2f2182050306070f95ae2ed2e30a831"),
     "profile": ((546672384 + 8760064) / 65536 ** 2, "psd.cu",
