@@ -44,6 +44,17 @@ KERNELS = {"auto": 0, "slope": 2, "parity": 4}
 # three-input xors (ALU pipe) and 20 32x32->64 multiplies (FMA pipe).
 ALU_OPS_PER_SITE_SWEEP = {"parity": 2 * 6 / 32 + 20 / 128,
                           "slope": 2 * 9 / 32 + 20 / 128}
+# Other thresholds (the batched, served and steady forms): both half-sweeps
+# test minima and maxima and flip (2 funnel shifts, 6 three-input ops and 2
+# ops per 32-site word and half-sweep), and every random level a 128-site
+# group needs costs one Philox block (20 three-input xors) and the comparison
+# steps with both thresholds (4 words x 3 ops). A group needs the deepest
+# comparison among its candidates of both half-sweeps (the levels are shared
+# between them): all k levels for k <= 3, else the expected maximum of
+# CANDIDATES_PER_GROUP_SWEEP depths (geometric with ratio 1/2, capped at k).
+CANDIDATES_PER_GROUP_SWEEP = 50  # minima + maxima per 128 sites and sweep: about 25
+                                 # per half-sweep on oracle states of the p = 0.95,
+                                 # q = 0.05 mix
 ALU_LANES_PER_SM = 64  # INT32 ALU-pipe lanes per SM per clock (16 per sub-partition)
 N_SMS = 152
 
@@ -62,6 +73,30 @@ TRAFFIC = {
     "profile": ((546672384 + 8760064) / 65536 ** 2, "psd.cu",
                 "3f9759eae0ced78fce621bcd7e32102d0a5400f4681801d3a991cb01838fd513"),
 }
+
+
+def alu_ops_per_attempt(okz, p, q, s_sel=0.5, k_max=32):
+    """Algorithmic ALU-pipe ops per site-update attempt for (p, q)."""
+    k, P, Q = okz.okz_thresholds(p, q, s_sel, k_max)
+    full = 1 << k
+    if k == 1 and 0 < P < full and Q == 0:
+        return ALU_OPS_PER_SITE_SWEEP["parity"]
+    if not any(0 < T < full for T in (P, Q)):
+        levels = 0.0
+    elif k <= 3:
+        levels = float(k)
+    else:
+        levels = sum(1.0 - (1.0 - 2.0 ** -m) ** CANDIDATES_PER_GROUP_SWEEP for m in range(k))
+    return 2 * 10 / 32 + levels * (20 + 12) / 128
+
+
+def alu_roofline(ops_per_attempt, attempts_per_s, peak, note):
+    """An ALU roofline record: algorithmic ops per attempt x attempts/s
+    against the measured ALU-pipe peak."""
+    achieved = ops_per_attempt * attempts_per_s / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak["value"], "unit": "Tops/s",
+            "frac": achieved / peak["value"], "ops_per_attempt": ops_per_attempt,
+            "peak_kind": "measured (okz_alu_peak)", "note": note}
 
 
 def _traffic(name, sites):
@@ -269,6 +304,7 @@ def run_reference(args, world, rank):
 
 
 def run_gpu(args, world, rank, local):
+    import numpy as np
     import torch
 
     import paper_1110_6745_gb300 as okz
@@ -364,13 +400,18 @@ def run_gpu(args, world, rank, local):
     host_planes.copy_(start_planes.cpu())
     del start_planes
 
+    restore_s = []
+
     def e2e_step():
+        t_r = time.perf_counter()
         sim.restore(host_planes, 0, 0)  # H2D inside the library, synchronous
+        restore_s.append(time.perf_counter() - t_r)
         sim.sweep(SWEEPS_PER_STEP)
         return sim.width2()
 
     e2e_step()
     torch.cuda.synchronize(dev)
+    restore_s.clear()
     _barrier(world)
     e2e_clocks = ClockSampler(local)
     e2e_clocks.start()
@@ -408,9 +449,16 @@ def run_gpu(args, world, rank, local):
     # served print the same as lines of their own)
     batched = served = None
     if not args.no_forms:
-        batched = batched_record(okz, args.budget_frac, args.plain_stride, rank, world)
+        batched = batched_record(okz, args.budget_frac, args.plain_stride, rank, world,
+                                 peak=peak_meas)
         from paper_1110_6745_gb300 import serve
         served = serve.served_record(UNIT)
+        reqs = serve.poisson_requests()
+        att = np.array([float(r.L) ** 2 * r.budget for r in reqs])
+        ops = np.array([alu_ops_per_attempt(okz, r.p, r.q) for r in reqs])
+        served["roofline"] = alu_roofline(
+            float((att * ops).sum() / att.sum()), served["value"] * 1e9, peak_meas,
+            "attempt-weighted over the request mix (p = 1, 0.75, 0.5: k = 1 minima only, 3, 2)")
     if rank != 0:
         return
     line = {
@@ -447,6 +495,10 @@ def run_gpu(args, world, rank, local):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": e2e_steps, "clocks": e2e_clk,
                 "ms_per_step": e2e_s / e2e_steps * 1e3,
+                # host clock around each synchronous okz_restore (the 4 GiB
+                # host-to-device copy and the conversion kernel)
+                "restore_ms_per_step": [r * 1e3 for r in restore_s],
+                "restore_h2d_gbs": [h2d / r / 1e9 for r in restore_s],
                 "path": "okz_restore(pinned host planes) + okz_sweep + okz_width2, "
                         "synchronous, no overlap between steps"},
         "w2_final": w2_final,
@@ -508,7 +560,7 @@ def replica_mix(n=4096, seed=2026):
     return L, T, seeds
 
 
-def batched_record(okz, frac, plain_stride, rank=0, world=1):
+def batched_record(okz, frac, plain_stride, rank=0, world=1, peak=None):
     """The batched workload: all 4096 replicas in one graph-captured
     persistent launch (tiling autotuned first) at budgets ceil(4 L^1.61)/frac,
     against per-replica plain launches (the in-place parity kernel, one
@@ -554,9 +606,7 @@ def batched_record(okz, frac, plain_stride, rank=0, world=1):
     plain = plain_attempts / plain_s / 1e9
     for s_ in sims:
         s_.close()
-    # algorithmic ALU-pipe work of the k = 32 mix is not fixed per attempt
-    # (the random levels are drawn lazily), so no roofline fraction is given
-    return {"value": batched, "unit": UNIT, "ms": ms, "replicas": n, "attempts": attempts,
+    rec = {"value": batched, "unit": UNIT, "ms": ms, "replicas": n, "attempts": attempts,
             "budgets": "ceil(4 L^1.61)/%d sweeps" % frac,
             "tiling": {"threads": tiling[0], "smem_bytes": tiling[1], "grid": tiling[2]},
             "autotune": tune,
@@ -568,6 +618,12 @@ def batched_record(okz, frac, plain_stride, rank=0, world=1):
                                   "seconds": plain_s},
             "batched_over_plain": batched / plain,
             "w2_mean_by_L": {int(l): float(np.nanmean(W2[L == l])) for l in np.unique(L)}}
+    if peak is not None:
+        rec["roofline"] = alu_roofline(
+            alu_ops_per_attempt(okz, 0.95, 0.05), batched * 1e9, peak,
+            "k = 32 with lazily drawn levels: about 7.0 levels per 128-site group and sweep "
+            "(the expected deepest of ~50 candidate comparisons)")
+    return rec
 
 
 def run_batched(args, world, rank, local):
@@ -576,7 +632,8 @@ def run_batched(args, world, rank, local):
 
     import paper_1110_6745_gb300 as okz
     torch.cuda.set_device(local)
-    rec = batched_record(okz, args.budget_frac, args.plain_stride, rank, world)
+    peak = measure_alu_peak(okz, local, None)
+    rec = batched_record(okz, args.budget_frac, args.plain_stride, rank, world, peak=peak)
     if rank != 0:
         return
     line = {
@@ -753,9 +810,12 @@ def run_steady(args, world, rank, local):
     import numpy as np
     import torch
 
+    import paper_1110_6745_gb300 as okz
     from paper_1110_6745_gb300.analysis import alpha_fss, steady_state_w2, w2_cumulants
 
     torch.cuda.set_device(local)
+    okz.lib()
+    peak = measure_alu_peak(okz, local, None)
     samples, ratios, attempts, secs = {}, {}, 0.0, {}
     _barrier(world)
     torch.cuda.synchronize()
@@ -785,6 +845,9 @@ def run_steady(args, world, rank, local):
         "w2_mean_by_L": {str(L): float(samples[L].mean()) for L in samples},
         "seconds_by_L": {str(L): secs[L] for L in secs},
         "alpha_fss": fss,
+        "roofline": alu_roofline(alu_ops_per_attempt(okz, 1.0, 0.0), world * attempts / dt, peak,
+                                 "whole run incl. burn-in, sampling and the exact W^2 per "
+                                 "sample; per GPU for n_gpus > 1 divide by n_gpus"),
         "kappa2_over_kappa1_sq": {str(L): float(ratios[L]) for L in ratios},
         "paper_alpha": "0.393(4), correction exponent 1.16 (Sec. III)",
     }
