@@ -447,8 +447,9 @@ def run_gpu(args, world, rank, local):
         small[name] = rec
     # the batched and served forms (compact records; --workload batched /
     # served print the same as lines of their own)
-    batched = served = None
+    batched = served = general_k = None
     if not args.no_forms:
+        general_k = general_k_record(okz, peak_meas)
         batched = batched_record(okz, args.budget_frac, args.plain_stride, rank, world,
                                  peak=peak_meas)
         from paper_1110_6745_gb300 import serve
@@ -509,6 +510,7 @@ def run_gpu(args, world, rank, local):
     if batched is not None:
         line["batched"] = batched
         line["served"] = served
+        line["general_k"] = general_k
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
         line["cpu_baseline_serial"] = cpu_serial_baseline()
@@ -558,6 +560,37 @@ def replica_mix(n=4096, seed=2026):
     T = np.ceil(4 * L.astype(np.float64) ** 1.61).astype(np.int64)
     seeds = (1000 + np.arange(n)).astype(np.uint64)
     return L, T, seeds
+
+
+def general_k_record(okz, peak, sweeps=64):
+    """One lattice through the general-k stream kernel (the large lattices of
+    the served form): L = 8192 and 4096 at p = 0.75, q = 0.25 (k = 3), the
+    library's tiling, 8 warm-up sweeps, then `sweeps` timed with CUDA events
+    on the simulation's stream."""
+    import torch
+    out = {}
+    for L in (8192, 4096):
+        stream = torch.cuda.Stream()
+        with torch.cuda.stream(stream):
+            sim = okz.Simulation(L, 0.75, 0.25, seed=31, kernel=okz.OKZ_KERNEL_PARITY_STREAM,
+                                 stream=stream.cuda_stream)
+        sim.sweep(8)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.sweep(sweeps)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        rate = float(L) * L * sweeps / (ms / 1e3)
+        out["L%d" % L] = {
+            "value": rate / 1e9, "unit": UNIT, "sweeps": sweeps, "ms": ms, "p": 0.75, "q": 0.25,
+            "k": 3, "words_per_thread": sim.wpt, "sweeps_per_pass": sim.fuse,
+            "band_rows": sim.band_rows,
+            "roofline": alu_roofline(alu_ops_per_attempt(okz, 0.75, 0.25), rate, peak,
+                                     "3 random levels per 128-site group and sweep; one "
+                                     "lattice alone on the GPU")}
+        sim.close()
+    return out
 
 
 def batched_record(okz, frac, plain_stride, rank=0, world=1, peak=None):

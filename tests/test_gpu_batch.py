@@ -156,3 +156,22 @@ def test_full_replica_mix_against_single_runs_and_oracle(okz, orc):
         ref.sweep(int(sweeps[r]))
         Sk, H0, t = got[r]
         assert Sk == ref.power_sums() and H0 == ref.H0 and t == ref.t, r
+
+
+@pytest.mark.parametrize("threads,smem", [(1024, 32 * 1024), (512, 64 * 1024), (256, 0)])
+def test_band_wavefront_sizes_match_single_runs(okz, threads, smem):
+    """The band wavefront at the sizes the replica mix does not reach: bands
+    that do not divide L (L = 384, 640: 3 and 5 groups a row), lattices swept
+    in global memory at 4096 and 8192 (bands of 4 rows at 256 threads), and
+    the k = 32, k = 3 and k = 1 acceptance paths, against runs of their own."""
+    cases = [(384, 0.95, 0.05, 21), (640, 0.75, 0.25, 22), (4096, 0.95, 0.05, 23),
+             (8192, 1.0, 0.0, 24), (8192, 0.5, 0.5, 25), (1152, 1.0, 1.0, 26)]
+    sweeps = [7, 5, 3, 2, 3, 6]
+    with okz.Batch([c[0] for c in cases], [c[1] for c in cases], [c[2] for c in cases],
+                   [c[3] for c in cases]) as b:
+        b.set_tiling(threads, smem)
+        b.run(sweeps)
+        for i, (L, p, q, seed) in enumerate(cases):
+            planes, H0, t, *_ = _single(okz, L, p, q, seed, sweeps[i])
+            bp, bH0, bt = b.state(i)
+            assert np.array_equal(bp, planes) and (bH0, bt) == (H0, t), (L, p, q)
