@@ -230,12 +230,103 @@ __device__ __forceinline__ void pstage(const uint32_t c[WPT], uint32_t lbit, uin
   }
 }
 
+// Thresholds of the general-k stage: P and Q with level 0 at bit 31, and the
+// comparison state every site starts from (lt: decided below, eq: undecided;
+// a threshold of 0 or 2^k decides every site at once).
+struct GenBits {
+  uint32_t pw, qw, lp0, ep0, lq0, eq0;
+};
+
+__device__ __forceinline__ GenBits gen_bits(const Accept &acc) {
+  const uint64_t full = 1ull << acc.k;
+  GenBits b;
+  b.pw = (uint32_t)(acc.P << (32 - acc.k));
+  b.qw = (uint32_t)(acc.Q << (32 - acc.k));
+  b.lp0 = (acc.P >= full) ? ~0u : 0u;
+  b.ep0 = (acc.P >= full || acc.P == 0) ? 0u : ~0u;
+  b.lq0 = (acc.Q >= full) ? ~0u : 0u;
+  b.eq0 = (acc.Q >= full || acc.Q == 0) ? 0u : ~0u;
+  return b;
+}
+
+__device__ __forceinline__ uint32_t rotl1(uint32_t x) { return __funnelshift_l(x, x, 1); }
+__device__ __forceinline__ uint32_t rotr1(uint32_t x) { return __funnelshift_r(x, x, 1); }
+
+// General k (random levels drawn lazily), one stage of half-sweep parity SP.
+// R6 keys a level by (group, sweep, level), never by the half-sweep, and a
+// site is active in one half-sweep only, so the levels the first half draws
+// for its candidates decide the second half's sites as far as they go. SP = 0
+// starts every site of the words undecided and draws levels while any lane
+// of the warp has an undecided candidate (every lane runs every stage, and a
+// warp runs to its last lane anyway); it leaves the second-half state packed
+// in LT, EQ (word j: the P comparison at the second-half positions, the Q
+// comparison rotated left by one bit into the first-half positions) with the
+// next level in m. SP = 1, one stream row later on the same row and sweep,
+// starts from that state and draws only the levels beyond it.
+template <int WPT, int SP>
+__device__ __forceinline__ void pstage_gen(const uint32_t c[WPT], uint32_t lbit, uint32_t rbit,
+                                           const uint32_t d[WPT], const uint32_t u[WPT],
+                                           uint32_t a, uint32_t g0, uint32_t t,
+                                           const RoundKeys &rk, const Accept &acc,
+                                           const GenBits &gb, uint32_t o[WPT], uint32_t *mn0,
+                                           uint32_t LT[WPT], uint32_t EQ[WPT], int &m) {
+  constexpr int NG = WPT / 4;
+  constexpr uint32_t kMin = SP ? 0x42u : 0x81u;
+  constexpr uint32_t kMax = SP ? 0x81u : 0x42u;
+  uint32_t mn[WPT], mx[WPT], lp[WPT], ep[WPT], lq[WPT], eq[WPT];
+#pragma unroll
+  for (int j = 0; j < WPT; ++j) {
+    const uint32_t l = __funnelshift_l(j == 0 ? (lbit << 31) : c[j - 1], c[j], 1);
+    const uint32_t r = __funnelshift_r(c[j], j == WPT - 1 ? rbit : c[j + 1], 1);
+    mn[j] = lop3<0x80>(lop3<kMin>(l, r, c[j]), lop3<kMin>(d[j], u[j], c[j]), a);
+    mx[j] = lop3<0x80>(lop3<kMax>(l, r, c[j]), lop3<kMax>(d[j], u[j], c[j]), a);
+    if (SP == 0) {
+      lp[j] = gb.lp0;
+      ep[j] = gb.ep0;
+      lq[j] = gb.lq0;
+      eq[j] = gb.eq0;
+    } else {  // only the second-half positions are read below
+      lp[j] = LT[j];
+      ep[j] = EQ[j];
+      lq[j] = rotr1(LT[j]);
+      eq[j] = rotr1(EQ[j]);
+    }
+  }
+  *mn0 = mn[0];
+  if (SP == 0) m = 0;
+  while (m < acc.k) {
+    uint32_t open = 0;
+#pragma unroll
+    for (int j = 0; j < WPT; ++j) open |= (ep[j] & mn[j]) | (eq[j] & mx[j]);
+    if (SP == 0 ? !__any_sync(0xFFFFFFFFu, open != 0u) : open == 0u) break;
+    const uint32_t pb = (gb.pw >> (31 - m)) & 1u, qb = (gb.qw >> (31 - m)) & 1u;
+#pragma unroll
+    for (int gq = 0; gq < NG; ++gq) {
+      const u32x4 b = philox10_rk(g0 + gq, 0u, t, (uint32_t)m, rk);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        lt_step(b.v[j], pb, lp[4 * gq + j], ep[4 * gq + j]);
+        lt_step(b.v[j], qb, lq[4 * gq + j], eq[4 * gq + j]);
+      }
+    }
+    ++m;
+  }
+#pragma unroll
+  for (int j = 0; j < WPT; ++j) o[j] = c[j] ^ ((lp[j] & mn[j]) | (lq[j] & mx[j]));
+  if (SP == 0) {
+#pragma unroll
+    for (int j = 0; j < WPT; ++j) {
+      LT[j] = (lp[j] & ~a) | (rotl1(lq[j]) & a);
+      EQ[j] = (ep[j] & ~a) | (rotl1(eq[j]) & a);
+    }
+  }
+}
+
 }  // namespace
 
 // SMALL: rows of at most 256 threads (L <= 32768 at 4 words per thread, any
 // L at 16), so the register budget is not capped by a 512- or 1024-thread
-// bound; in the general-k mode the 4-word kernels also carry random levels 1
-// and 2 between half-sweeps.
+// bound.
 template <int WPT, int F, int MODE, bool SMALL>
 __global__ void __launch_bounds__(SMALL ? 256 : (WPT == 4 ? 1024 : 512), 1)
 parity_stream_kernel(const uint32_t *__restrict__ src, uint32_t *__restrict__ dst, int L,
@@ -244,7 +335,9 @@ parity_stream_kernel(const uint32_t *__restrict__ src, uint32_t *__restrict__ ds
   constexpr int NST = 2 * F;
   constexpr int NC = NST > 1 ? NST - 1 : 1;  // stages whose output is carried
   constexpr int NG = WPT / 4;
-  constexpr int KC = (SMALL && MODE == kPModeGen && WPT == 4) ? 3 : 1;  // levels drawn once per sweep
+  constexpr bool GEN = MODE == kPModeGen;
+  constexpr int KC = 1;            // k <= 1: level 0 drawn once per sweep
+  constexpr int FG = GEN ? F : 1;  // general k: comparison state carried per sweep
   extern __shared__ __align__(128) unsigned char smem[];
   const int nthr = blockDim.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -283,7 +376,10 @@ parity_stream_kernel(const uint32_t *__restrict__ src, uint32_t *__restrict__ ds
 
   uint32_t Wd[NC][WPT], Wc[NC][WPT];  // stage h's outputs two / one steps ago
   uint32_t WL[NC], WR[NC];            // x-neighbour bits of Wc[h]
-  uint32_t R[F][KC][WPT];             // levels 0..KC-1 of the row stage 2j saw last step
+  uint32_t R[F][KC][WPT];             // k <= 1: level 0 of the row stage 2j saw last step
+  uint32_t CL[FG][WPT], CE[FG][WPT];  // general k: that row's packed second-half state
+  int Cm[FG];
+  const GenBits gb = gen_bits(acc);
 #pragma unroll
   for (int h = 0; h < NC; ++h) {
     WL[h] = 0;
@@ -300,6 +396,15 @@ parity_stream_kernel(const uint32_t *__restrict__ src, uint32_t *__restrict__ ds
     for (int m = 0; m < KC; ++m)
 #pragma unroll
       for (int j = 0; j < WPT; ++j) R[q][m][j] = 0;
+#pragma unroll
+  for (int q = 0; q < FG; ++q) {
+    Cm[q] = 0;
+#pragma unroll
+    for (int j = 0; j < WPT; ++j) {
+      CL[q][j] = 0;
+      CE[q][j] = 0;
+    }
+  }
 
   const uint32_t w0 = (uint32_t)(WPT * tid);
   const uint32_t wprev = (w0 == 0) ? W - 1 : w0 - 1;
@@ -339,22 +444,20 @@ parity_stream_kernel(const uint32_t *__restrict__ src, uint32_t *__restrict__ ds
       const uint32_t lb = *(const uint32_t *)(rc + 4 * wprev) >> 31;
       const uint32_t rb = *(const uint32_t *)(rc + 4 * wnext) & 1u;
       uint32_t Rn[F][KC][WPT];
+      uint32_t CnL[FG][WPT], CnE[FG][WPT];
+      int Cnm[FG];
 #pragma unroll
       for (int h = 0; h < NST; ++h) {
         const int s = h & 1;
         const uint32_t t = t0 + (uint32_t)(h >> 1);
         uint32_t g0 = gq0 - (uint32_t)h * groups_per_row;  // row y-1-h, wrapped
         if (q0 < h) g0 += wrap_groups;
-        if (s == 0) {  // fresh words of row y-1-h, sweep t: level 0, and 1..KC-1 if k needs them
+        if (!GEN && s == 0) {  // fresh words of row y-1-h, sweep t: level 0
 #pragma unroll
-          for (int m = 0; m < KC; ++m) {
-            if (m > 0 && m >= acc.k) break;
+          for (int gq = 0; gq < NG; ++gq) {
+            const u32x4 b = philox10_rk(g0 + gq, 0u, t, 0u, rk);
 #pragma unroll
-            for (int gq = 0; gq < NG; ++gq) {
-              const u32x4 b = philox10_rk(g0 + gq, 0u, t, (uint32_t)m, rk);
-#pragma unroll
-              for (int j = 0; j < 4; ++j) Rn[h >> 1][m][4 * gq + j] = b.v[j];
-            }
+            for (int j = 0; j < 4; ++j) Rn[h >> 1][0][4 * gq + j] = b.v[j];
           }
         }
         const uint32_t *c = (h == 0) ? cc : Wc[h > 0 ? h - 1 : 0];
@@ -363,8 +466,14 @@ parity_stream_kernel(const uint32_t *__restrict__ src, uint32_t *__restrict__ ds
         const uint32_t lbit = (h == 0) ? lb : WL[h > 0 ? h - 1 : 0];
         const uint32_t rbit = (h == 0) ? rb : WR[h > 0 ? h - 1 : 0];
         uint32_t o[WPT];
-        // s = 1 uses the words of the same row drawn by stage h-1 last step
-        if (s == 0)
+        // s = 1 uses what stage h-1 drew for the same row last step
+        if (GEN && s == 0)
+          pstage_gen<WPT, 0>(c, lbit, rbit, d, u, am, g0, t, rk, acc, gb, o, &mn0[h],
+                             CnL[(h >> 1) % FG], CnE[(h >> 1) % FG], Cnm[(h >> 1) % FG]);
+        else if (GEN)
+          pstage_gen<WPT, 1>(c, lbit, rbit, d, u, am, g0, t, rk, acc, gb, o, &mn0[h],
+                             CL[(h >> 1) % FG], CE[(h >> 1) % FG], Cm[(h >> 1) % FG]);
+        else if (s == 0)
           pstage<WPT, MODE, 0, KC>(c, lbit, rbit, d, u, am, Rn[h >> 1], g0, t, rk, acc, md,
                                    o, &mn0[h]);
         else
@@ -373,7 +482,15 @@ parity_stream_kernel(const uint32_t *__restrict__ src, uint32_t *__restrict__ ds
         fbit[h] = (o[0] ^ c[0]) & 1u;
 #pragma unroll
         for (int j = 0; j < WPT; ++j) out[h][j] = o[j];
-        if (s == 1) {
+        if (s == 1 && GEN) {
+          const int q = (h >> 1) % FG;
+          Cm[q] = Cnm[q];
+#pragma unroll
+          for (int j = 0; j < WPT; ++j) {
+            CL[q][j] = CnL[q][j];
+            CE[q][j] = CnE[q][j];
+          }
+        } else if (s == 1) {
 #pragma unroll
           for (int m = 0; m < KC; ++m)
 #pragma unroll
