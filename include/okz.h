@@ -271,7 +271,9 @@ okz_status okz_restore(okz_sim *sim, const uint32_t *planes, int in_is_device,
  * CUDA events, and keeps the fastest per sweep. The choice is remembered for
  * (device, L, kernel, acceptance mode: k = 1 with minima only, other k <= 1,
  * k >= 2) and used by every later okz_create / okz_create_ex that leaves
- * words_per_thread, sweeps_per_pass and band_rows automatic (0). Results are
+ * words_per_thread and sweeps_per_pass automatic (0), band_rows too when that
+ * is 0 (a band_rows given with a tuned two-sweep pass it does not fit makes
+ * the pass one sweep). Results are
  * bit-identical for every tiling, so tuning never changes a result. Writes
  * the choice and its time per sweep (any output may be NULL). Synchronizing; each scratch simulation holds
  * okz_device_bytes(L) for its run. Errors: EINVAL, EUNSUPPORTED (L outside the

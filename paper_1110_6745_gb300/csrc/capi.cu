@@ -260,12 +260,13 @@ okz_status okz_create_ex(const okz_params *prm, void *dev_buf, size_t bytes, voi
     return OKZ_EUNSUPPORTED;
   }
   int wpt = prm->words_per_thread, fuse = prm->sweeps_per_pass, band = prm->band_rows;
-  if (streamed && wpt == 0 && fuse == 0 && band == 0) {  // okz_tune_stream's best tiling
+  if (streamed && wpt == 0 && fuse == 0) {  // okz_tune_stream's best tiling
     int tw = 0, tf = 0, tb = 0;
     if (tuned_tiling(prm->L, kernel, stream_mode(k, P, Q), &tw, &tf, &tb)) {
       wpt = tw;
       fuse = tf;
-      band = tb;
+      if (band == 0) band = tb;
+      else if (band < stream_min_band(fuse)) fuse = 1;  // the caller's band decides
     }
   }
   if (streamed) {
