@@ -543,7 +543,8 @@ def growth_line(okz, L, T, nsamp, seed, reps=3):
             "samples": len(times), "ms_per_run": best * 1e3,
             "us_per_sample": best * 1e6 / len(times), "w2_final": w2_last,
             "kernel": {1: "slope plain", 2: "slope stream", 3: "parity plain",
-                       4: "parity stream"}[info.kernel],
+                       4: "parity stream", 5: "parity one-CTA (shared memory, one launch per "
+                                              "sample interval)"}[info.kernel],
             "words_per_thread": info.words_per_thread, "sweeps_per_pass": info.sweeps_per_pass,
             "graph_chunk": info.graph_chunk, "graph_replays_per_run": info.graph_replays,
             "timing": "host clock around the whole run (sweeps and synchronous W^2 "

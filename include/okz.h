@@ -80,13 +80,18 @@ typedef struct okz_i128 {
  *    ((x+y) mod 2) == 0, likewise sigma_y), and a move toggles only the
  *    site's own bit: one bit read and one written per site and sweep.
  * AUTO picks PARITY_STREAM when L is a multiple of 4096 and at most
- * 131072, else PARITY_PLAIN. */
+ * 131072, else PARITY_CTA up to L = 512 (L % 32 == 0), else PARITY_PLAIN. */
 enum {
     OKZ_KERNEL_AUTO = 0,
     OKZ_KERNEL_PLAIN = 1,          /* slope planes, one in-place launch per half-sweep */
     OKZ_KERNEL_STREAM = 2,         /* slope planes, TMA-staged rows, ping-pong         */
     OKZ_KERNEL_PARITY_PLAIN = 3,   /* parity plane, one in-place launch per half-sweep */
-    OKZ_KERNEL_PARITY_STREAM = 4   /* parity plane, TMA-staged rows, ping-pong         */
+    OKZ_KERNEL_PARITY_STREAM = 4,  /* parity plane, TMA-staged rows, ping-pong         */
+    OKZ_KERNEL_PARITY_CTA = 5      /* parity plane swept by one CTA out of shared
+                                      memory, all sweeps of a call in one launch;
+                                      L % 32 == 0 and L <= 1024. AUTO: the stream
+                                      kernel where it runs (L % 4096 == 0), else
+                                      this one up to L = 512, else PARITY_PLAIN     */
 };
 
 typedef struct okz_params {
@@ -127,7 +132,8 @@ typedef struct okz_info {
 typedef struct okz_sim okz_sim;
 
 /* Fills *prm with the defaults: L = 0, p = 1, q = 0, seed = 0, s_sel = 0.5,
- * k_max = 32, kernel = AUTO, words_per_thread = 0, sweeps_per_pass = 0. The
+ * k_max = 32, kernel = AUTO, words_per_thread = 0, sweeps_per_pass = 0,
+ * band_rows = 0. The
  * last two only choose how the stream kernel tiles the work; results are
  * bit-identical for every choice. 8 words per thread needs L % 8192 == 0,
  * 16 (parity stream kernel only) L % 16384 == 0. Their automatic values

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libokz.so")
 OKZ_OK, OKZ_EINVAL, OKZ_ENOMEM, OKZ_ECUDA, OKZ_ETIMEOUT, OKZ_EBUSY, OKZ_EOVERFLOW, \
     OKZ_EUNSUPPORTED = range(8)
 OKZ_KERNEL_AUTO, OKZ_KERNEL_PLAIN, OKZ_KERNEL_STREAM = 0, 1, 2
-OKZ_KERNEL_PARITY_PLAIN, OKZ_KERNEL_PARITY_STREAM = 3, 4
+OKZ_KERNEL_PARITY_PLAIN, OKZ_KERNEL_PARITY_STREAM, OKZ_KERNEL_PARITY_CTA = 3, 4, 5
 STATUS_NAMES = {0: "OKZ_OK", 1: "OKZ_EINVAL", 2: "OKZ_ENOMEM", 3: "OKZ_ECUDA",
                 4: "OKZ_ETIMEOUT", 5: "OKZ_EBUSY", 6: "OKZ_EOVERFLOW", 7: "OKZ_EUNSUPPORTED"}
 

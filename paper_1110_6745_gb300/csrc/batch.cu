@@ -593,6 +593,54 @@ cudaError_t launch_batch_moments(const uint32_t *arena, SlotDesc *slots, const W
   return cudaGetLastError();
 }
 
+// One lattice swept in place by one CTA out of shared memory: the band
+// wavefront of the batch kernel (bit-identical to every other sweep kernel),
+// all n sweeps in one launch. For lattices too small to spread over the GPU,
+// where a launch per half-sweep costs more than the sweep itself.
+__global__ void __launch_bounds__(1024, 1)
+cta_lattice_kernel(uint32_t *__restrict__ B, int L, uint32_t t0, int n, uint64_t seed, Accept acc,
+                   Ctrl *__restrict__ ctrl) {
+  extern __shared__ __align__(16) uint32_t sm[];
+  __shared__ __align__(8) uint32_t rks[20];
+  __shared__ BandCarry carry;
+  const uint32_t words = (uint32_t)L * (uint32_t)(L >> 5);
+  if (threadIdx.x < 10) {
+    const uint32_t r = threadIdx.x;
+    rks[2 * r] = (uint32_t)seed + r * kPhiloxWeylA;
+    rks[2 * r + 1] = (uint32_t)(seed >> 32) + r * kPhiloxWeylB;
+  }
+  for (uint32_t w = threadIdx.x; w < words; w += blockDim.x) sm[w] = B[w];
+  __syncthreads();
+  int dH0 = 0;
+  cta_sweeps<1>(sm, L, t0, n, rks, acc, dH0, carry);
+  for (uint32_t w = threadIdx.x; w < words; w += blockDim.x) B[w] = sm[w];
+  if (threadIdx.x == 0) ctrl->H0 += dH0;  // thread 0 owns site (0,0)
+}
+
+bool cta_kernel_supports(int64_t L) { return L >= 32 && L % 32 == 0 && L <= kCtaMaxL; }
+
+cudaError_t launch_cta_sweeps(uint32_t *B, int64_t L, uint32_t t, int64_t n, uint64_t seed,
+                              const Accept &acc, Ctrl *ctrl, cudaStream_t st) {
+  const size_t smem = (size_t)L * (size_t)L / 8;
+  // threads: one per 128-site group, whole warps, at least 2 groups' rows
+  int threads = (int)((L * (L / 32) / 4 + 31) / 32 * 32);
+  if (threads > 1024) threads = 1024;
+  if (threads < 64) threads = 64;
+  cudaError_t e = cudaFuncSetAttribute((const void *)cta_lattice_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)((size_t)kCtaMaxL * kCtaMaxL / 8));
+  if (e != cudaSuccess) return e;
+  for (int64_t done = 0; done < n;) {  // launches of at most 2^20 sweeps
+    const int64_t m = (n - done < (1 << 20)) ? n - done : (1 << 20);
+    cta_lattice_kernel<<<1, threads, smem, st>>>(B, (int)L, t + (uint32_t)done, (int)m, seed, acc,
+                                                 ctrl);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    done += m;
+  }
+  return cudaSuccess;
+}
+
 int batch_occupancy(int threads, size_t smem_bytes) {
   int per_sm = 0;
   const void *fn = threads > 512   ? (const void *)batch_sweep_kernel<1024, 1>

@@ -248,11 +248,17 @@ okz_status okz_create_ex(const okz_params *prm, void *dev_buf, size_t bytes, voi
   st = okz_thresholds(prm->p, prm->q, prm->s_sel, prm->k_max, &k, &P, &Q);
   if (st != OKZ_OK) return st;
   int kernel = prm->kernel;
-  if (kernel == OKZ_KERNEL_AUTO)
-    kernel = stream_kernel_supports(prm->L) ? OKZ_KERNEL_PARITY_STREAM : OKZ_KERNEL_PARITY_PLAIN;
-  if (kernel < OKZ_KERNEL_PLAIN || kernel > OKZ_KERNEL_PARITY_STREAM) {
+  if (kernel == OKZ_KERNEL_AUTO)  // one CTA up to L = 512 (measured: 2.3x faster at 256)
+    kernel = stream_kernel_supports(prm->L)      ? OKZ_KERNEL_PARITY_STREAM
+             : (prm->L <= 512 && cta_kernel_supports(prm->L)) ? OKZ_KERNEL_PARITY_CTA
+                                                              : OKZ_KERNEL_PARITY_PLAIN;
+  if (kernel < OKZ_KERNEL_PLAIN || kernel > OKZ_KERNEL_PARITY_CTA) {
     set_error("unknown kernel selector");
     return OKZ_EINVAL;
+  }
+  if (kernel == OKZ_KERNEL_PARITY_CTA && !cta_kernel_supports(prm->L)) {
+    set_error("the one-CTA kernel needs L % 32 == 0 and L <= 1024");
+    return OKZ_EUNSUPPORTED;
   }
   const bool streamed = kernel == OKZ_KERNEL_STREAM || kernel == OKZ_KERNEL_PARITY_STREAM;
   if (streamed && !stream_kernel_supports(prm->L)) {
@@ -327,7 +333,8 @@ okz_status okz_create_ex(const okz_params *prm, void *dev_buf, size_t bytes, voi
   sim->acc.Q = Q;
   sim->acc.k = k;
   sim->kernel = kernel;
-  sim->parity = kernel == OKZ_KERNEL_PARITY_PLAIN || kernel == OKZ_KERNEL_PARITY_STREAM;
+  sim->parity = kernel == OKZ_KERNEL_PARITY_PLAIN || kernel == OKZ_KERNEL_PARITY_STREAM ||
+                kernel == OKZ_KERNEL_PARITY_CTA;
   sim->wpt = wpt;
   sim->fuse = fuse;
   sim->band_rows = band;
@@ -470,6 +477,14 @@ okz_status okz_sweep(okz_sim *sim, int64_t n) {
     return OKZ_EOVERFLOW;
   }
   const int64_t L = sim->prm.L;
+  if (sim->kernel == OKZ_KERNEL_PARITY_CTA) {  // every sweep of the call in one launch
+    if (n == 0) return OKZ_OK;
+    cudaError_t e = launch_cta_sweeps(sim->planes[sim->cur], L, (uint32_t)sim->t, n,
+                                      sim->prm.seed, sim->acc, sim->ctrl, sim->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "sweep launch");
+    sim->t += (uint64_t)n;
+    return OKZ_OK;
+  }
   int64_t done = 0;
   const bool inplace = sim->kernel == OKZ_KERNEL_PLAIN || sim->kernel == OKZ_KERNEL_PARITY_PLAIN;
   if (inplace && n >= kGraphChunk) {  // whole chunks by graph replay
@@ -516,8 +531,8 @@ okz_status okz_sweep_rs(okz_sim *sim, int64_t n) {
     return OKZ_EINVAL;
   }
   if (!sim->parity) {
-    set_error("okz_sweep_rs needs a parity-plane simulation (kernel PARITY_PLAIN or "
-              "PARITY_STREAM)");
+    set_error("okz_sweep_rs needs a parity-plane simulation (kernel PARITY_PLAIN, "
+              "PARITY_STREAM or PARITY_CTA)");
     return OKZ_EUNSUPPORTED;
   }
   if (sim->prm.L % 32 != 0) {

@@ -71,6 +71,13 @@ inline int stream_grid(int L, int F, int band_rows, int capacity) {
   return grid < 1 ? 1 : grid;
 }
 
+// One-CTA kernel (batch.cu): the parity plane swept out of shared memory,
+// n sweeps in one launch; L % 32 == 0 and L <= kCtaMaxL (128 KiB).
+constexpr int64_t kCtaMaxL = 1024;
+bool cta_kernel_supports(int64_t L);
+cudaError_t launch_cta_sweeps(uint32_t *B, int64_t L, uint32_t t, int64_t n, uint64_t seed,
+                              const Accept &acc, Ctrl *ctrl, cudaStream_t st);
+
 // The parity stream kernel also takes 16 words per thread: L % 16384 == 0.
 bool parity_wpt_valid(int64_t L, int wpt);
 cudaError_t launch_parity_stream(const uint32_t *src, uint32_t *dst, int64_t L, uint32_t t,

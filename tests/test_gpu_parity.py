@@ -46,9 +46,10 @@ MODES = [  # p, q, s_sel: k and kernel path
 
 PLAIN_KINDS = [1, 3]   # OKZ_KERNEL_PLAIN (slope planes), OKZ_KERNEL_PARITY_PLAIN
 STREAM_KINDS = [2, 4]  # OKZ_KERNEL_STREAM, OKZ_KERNEL_PARITY_STREAM
+SMALL_KINDS = [1, 3, 5]  # in-place kinds and OKZ_KERNEL_PARITY_CTA (one CTA, L <= 1024)
 
 
-@pytest.mark.parametrize("kernel", PLAIN_KINDS)
+@pytest.mark.parametrize("kernel", SMALL_KINDS)
 @pytest.mark.parametrize("L", [32, 64, 96, 128, 256, 480])
 @pytest.mark.parametrize("p,q,s_sel", MODES)
 def test_plain_kernel_matches_oracle(okz, orc, L, p, q, s_sel, kernel):
@@ -238,7 +239,7 @@ def test_stream_equals_plain_long_run(okz, L, kernel):
 
 
 @pytest.mark.parametrize("L,kernel", [(64, 1), (256, 1), (4096, 2), (64, 3), (256, 3),
-                                      (4096, 4)])
+                                      (4096, 4), (256, 5), (1024, 5)])
 def test_moments_and_heights_match_oracle(okz, orc, L, kernel):
     ref = orc.Sim(L, 0.95, 0.05, 3)
     with okz.Simulation(L, 0.95, 0.05, seed=3, kernel=kernel) as sim:
@@ -255,17 +256,17 @@ def test_moments_and_heights_match_oracle(okz, orc, L, kernel):
         assert np.array_equal(sim.heights(y0=L // 2 - 3, ny=5), h[L // 2 - 3:L // 2 + 2])
 
 
-@pytest.mark.parametrize("kernel", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("kernel", [0, 1, 2, 3, 4, 5])
 def test_flat_start_width(okz, kernel):
     for L in (32, 256, 4096):
-        if kernel in (2, 4) and L < 4096:
+        if (kernel in (2, 4) and L < 4096) or (kernel == 5 and L > 1024):
             continue
         with okz.Simulation(L, 1.0, 0.0, seed=1, kernel=kernel) as sim:
             S1, S2, W2 = sim.width2()
             assert W2 == 0.25 and S1 == L * L // 2 and S2 == L * L // 2
 
 
-@pytest.mark.parametrize("kernel", PLAIN_KINDS)
+@pytest.mark.parametrize("kernel", SMALL_KINDS)
 def test_growth_series_L256(okz, orc, kernel):
     """L = 256, p = 1, q = 0, seed 1, 1000 sweeps, W^2 at 20 log-spaced times:
     every record equal to the oracle's."""
@@ -299,6 +300,26 @@ def test_inplace_sweeps_by_graph_replay(okz, orc, L, p, q, kernel):
             assert (info.graph_chunk, info.graph_replays) == (32, replays)
             S1, S2, W2 = sim.width2()
             assert (S1, S2) == ref.sums() and W2 == ref.width2()
+
+
+@pytest.mark.parametrize("L,p,q,n", [(1024, 0.95, 0.05, 40), (512, 0.75, 0.25, 300),
+                                     (384, 1.0, 1.0, 1000)])
+def test_one_cta_kernel_long_calls(okz, orc, L, p, q, n):
+    """The one-CTA kernel runs every sweep of a call in one launch: long
+    calls at the largest sizes it takes, against the oracle."""
+    ref = orc.Sim(L, p, q, 77)
+    with okz.Simulation(L, p, q, seed=77, kernel=okz.OKZ_KERNEL_PARITY_CTA) as sim:
+        ref.sweep(n)
+        sim.sweep(n)
+        _compare(sim, ref)
+        assert sim.width2()[2] == ref.width2()
+
+
+def test_one_cta_kernel_size_rule(okz):
+    for L in (2048, 1000):
+        with pytest.raises(okz.OkzError) as e:
+            okz.Simulation(L, 1.0, 0.0, seed=1, kernel=okz.OKZ_KERNEL_PARITY_CTA)
+        assert e.value.status == okz.OKZ_EUNSUPPORTED
 
 
 def test_growth_series_helper_matches_oracle(okz, orc):
