@@ -520,9 +520,10 @@ def run_gpu(args, world, rank, local):
 def growth_line(okz, L, T, nsamp, seed, reps=3):
     """A whole growth run as the paper times it (Sec. III): the striped start
     swept to n log-spaced sample times over T sweeps, the exact W^2 taken at
-    every sample (host-synchronous: each sample's sums are read back). Timed
-    on the host clock from t = 0, best of `reps` runs after one untimed run.
-    Returns attempts/s and the time per run and per sample."""
+    every sample, through okz_growth_series (sweeps and measurements queued
+    on the device, each sample's sums kept there, one read-back at the end).
+    Timed on the host clock from t = 0, best of `reps` runs after one untimed
+    run. Returns attempts/s and the time per run and per sample."""
     from paper_1110_6745_gb300.analysis import sample_times
     times = sample_times(T, nsamp)
     best, info, w2_last = None, None, None
@@ -530,12 +531,9 @@ def growth_line(okz, L, T, nsamp, seed, reps=3):
         with okz.Simulation(L, 1.0, 0.0, seed=seed) as sim:
             sim.width2()  # the lattice is initialised before the clock starts
             t0 = time.perf_counter()
-            done = 0
-            for t in times:
-                sim.sweep(t - done)
-                done = t
-                w2_last = sim.width2()[2]
+            rec = sim.growth_series(times)
             dt = time.perf_counter() - t0
+            w2_last = rec[-1][4]
             info = sim.info()
         if rep > 0 and (best is None or dt < best):
             best = dt
@@ -547,8 +545,9 @@ def growth_line(okz, L, T, nsamp, seed, reps=3):
                                               "sample interval)"}[info.kernel],
             "words_per_thread": info.words_per_thread, "sweeps_per_pass": info.sweeps_per_pass,
             "graph_chunk": info.graph_chunk, "graph_replays_per_run": info.graph_replays,
-            "timing": "host clock around the whole run (sweeps and synchronous W^2 "
-                      "samples), best of %d" % reps}
+            "timing": "host clock around the whole run (okz_growth_series: sweeps and "
+                      "exact W^2 samples queued on the device, one synchronisation), "
+                      "best of %d" % reps}
 
 
 def replica_mix(n=4096, seed=2026):

@@ -213,6 +213,17 @@ okz_status okz_width2(okz_sim *sim, okz_i128 *S1, okz_i128 *S2, double *W2);
 okz_status okz_moments(okz_sim *sim, okz_i128 Sk[4], double *W2, double *skew,
                        double *kurt);
 
+/* The growth run of Sec. III in one call: sweeps the simulation to each of
+ * the n sample times (ascending from its current sweep count) and takes at
+ * each the exact S1 = sum h, S2 = sum h^2 and W^2 of okz_width2 (Eq. (4))
+ * and H0 = h(0,0). Sweeps and measurements are queued on the simulation's
+ * stream; each sample's sums are copied aside on the device, and the call
+ * synchronizes once at the end. Outputs are host arrays of n entries (any may
+ * be NULL). Errors: EINVAL (times not ascending), EOVERFLOW (a time past
+ * 2^32 - 1), ENOMEM, ECUDA, ETIMEOUT. */
+okz_status okz_growth_series(okz_sim *sim, int32_t n, const uint64_t *times, okz_i128 *S1,
+                             okz_i128 *S2, double *W2, int64_t *H0);
+
 /* okz_moments in two halves, for callers that must not block while other
  * streams work: okz_moments_enqueue launches the power-sum kernels on the
  * simulation's stream and returns at once; okz_moments_fetch waits for that

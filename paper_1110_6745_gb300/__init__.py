@@ -66,6 +66,7 @@ _SIGS = {
                                  _c.POINTER(_vp)]),
     "okz_sweep": (_c.c_int, [_vp, _c.c_int64]),
     "okz_sweep_rs": (_c.c_int, [_vp, _c.c_int64]),
+    "okz_growth_series": (_c.c_int, [_vp, _c.c_int32, _vp, _vp, _vp, _vp, _vp]),
     "okz_width2": (_c.c_int, [_vp, _c.POINTER(okz_i128), _c.POINTER(okz_i128),
                               _c.POINTER(_c.c_double)]),
     "okz_moments": (_c.c_int, [_vp, _c.POINTER(okz_i128), _c.POINTER(_c.c_double),
@@ -196,6 +197,23 @@ def okz_width2(h):
     _check(lib().okz_width2(h, ctypes.byref(S1), ctypes.byref(S2), ctypes.byref(W2)),
            "okz_width2")
     return S1.value(), S2.value(), W2.value
+
+
+def okz_growth_series(h, times):
+    """Sweeps to each sample time and takes the exact sums there in one call
+    (one synchronisation) -> [(t, H0, S1, S2, W2)] with S1 = sum h and
+    S2 = sum h^2 as Python ints."""
+    times = np.ascontiguousarray(np.asarray(times, dtype=np.uint64))
+    n = len(times)
+    S1 = (okz_i128 * max(n, 1))()
+    S2 = (okz_i128 * max(n, 1))()
+    W2 = np.zeros(max(n, 1), np.float64)
+    H0 = np.zeros(max(n, 1), np.int64)
+    _check(lib().okz_growth_series(h, n, times.ctypes.data, ctypes.addressof(S1),
+                                   ctypes.addressof(S2), W2.ctypes.data, H0.ctypes.data),
+           "okz_growth_series")
+    return [(int(times[i]), int(H0[i]), S1[i].value(), S2[i].value(), float(W2[i]))
+            for i in range(n)]
 
 
 def okz_selftest_wait_timeout(stream=None):
@@ -407,6 +425,10 @@ class Simulation:
 
     def synchronize(self):
         okz_synchronize(self.h)
+
+    def growth_series(self, times):
+        """[(t, H0, S1, S2, W2)] at every sample time, in one call."""
+        return okz_growth_series(self.h, times)
 
     @property
     def stream(self):

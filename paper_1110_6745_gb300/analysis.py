@@ -186,15 +186,9 @@ def growth_series(L, T, n, p=1.0, q=0.0, seed=0, s_sel=0.5, kernel=None):
     sample time of sample_times(T, n); returns records (t, H0, S1, S2, W2)
     with the exact sums of h and h^2 (Eq. (4))."""
     kw = {} if kernel is None else {"kernel": kernel}
-    rec = []
     with okz.Simulation(L, p, q, seed=seed, s_sel=s_sel, **kw) as sim:
-        done = 0
-        for t in sample_times(T, n):
-            sim.sweep(t - done)
-            done = t
-            S1, S2, W2 = sim.width2()
-            rec.append((t, sim.info().H0, S1, S2, W2))
-    return rec
+        # sweeps and exact sums queued on the device, one synchronisation
+        return [tuple(r) for r in sim.growth_series(sample_times(T, n))]
 
 
 def beta_fit(t, w2, tmin, tmax, w2_0=0.25):

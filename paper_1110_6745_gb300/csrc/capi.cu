@@ -6,6 +6,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <cstddef>
+#include <vector>
 #include <map>
 #include <mutex>
 #include <new>
@@ -622,6 +624,63 @@ okz_status okz_width2(okz_sim *sim, okz_i128 *S1, okz_i128 *S2, double *W2) {
   if (S1) *S1 = from_i128(S[0] + N * h0);
   if (S2) *S2 = from_i128(S[1] + 2 * h0 * S[0] + N * h0 * h0);
   if (W2) *W2 = w2;
+  return OKZ_OK;
+}
+
+okz_status okz_growth_series(okz_sim *sim, int32_t n, const uint64_t *times, okz_i128 *S1,
+                             okz_i128 *S2, double *W2, int64_t *H0) {
+  if (!sim || n < 0 || (n > 0 && !times)) {
+    set_error("okz_growth_series: null simulation, negative count or null times");
+    return OKZ_EINVAL;
+  }
+  for (int32_t i = 0; i < n; ++i) {
+    if (times[i] < (i ? times[i - 1] : sim->t)) {
+      set_error("okz_growth_series: sample times must ascend from the current sweep count");
+      return OKZ_EINVAL;
+    }
+    if (times[i] > 0xFFFFFFFFull) {
+      set_error("sweep counter would pass 2^32 - 1");
+      return OKZ_EOVERFLOW;
+    }
+  }
+  if (n == 0) return OKZ_OK;
+  // each sample's H0 and sums (the control block's first 80 bytes) are copied
+  // aside on the device; one read-back and one synchronisation at the end
+  constexpr size_t kRec = offsetof(Ctrl, sum) + sizeof(((Ctrl *)nullptr)->sum);
+  void *dev = nullptr;
+  cudaError_t e = scratch_alloc(&dev, (size_t)n * kRec, sim->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "okz_growth_series scratch");
+  okz_status st = OKZ_OK;
+  for (int32_t i = 0; i < n && st == OKZ_OK && e == cudaSuccess; ++i) {
+    st = okz_sweep(sim, (int64_t)(times[i] - sim->t));
+    if (st != OKZ_OK) break;
+    e = launch_power_sums(sim->planes[sim->cur], sim->prm.L, sim->parity, 2, sim->hcol,
+                          sim->partials, sim->ctrl, sim->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync((char *)dev + (size_t)i * kRec, sim->ctrl, kRec,
+                          cudaMemcpyDeviceToDevice, sim->stream);
+  }
+  std::vector<unsigned char> host((size_t)n * kRec);
+  if (st == OKZ_OK && e == cudaSuccess)
+    e = cudaMemcpyAsync(host.data(), dev, host.size(), cudaMemcpyDeviceToHost, sim->stream);
+  scratch_free(dev, sim->stream);
+  if (st != OKZ_OK) return st;
+  if (e != cudaSuccess) return cuda_fail(e, "okz_growth_series");
+  st = sync_and_check(sim);
+  if (st != OKZ_OK) return st;
+  const __int128 N = (__int128)sim->prm.L * sim->prm.L;
+  for (int32_t i = 0; i < n; ++i) {
+    Ctrl c;
+    memcpy(&c, host.data() + (size_t)i * kRec, kRec);
+    const __int128 s1 = (__int128)(((unsigned __int128)c.sum[1] << 64) | c.sum[0]);
+    const __int128 s2 = (__int128)(((unsigned __int128)c.sum[3] << 64) | c.sum[2]);
+    const __int128 h0 = c.H0;
+    // as okz_width2: sums about H0, the numerator N S2 - S1^2 shift-free
+    if (W2) W2[i] = (double)(N * s2 - s1 * s1) / ((double)N * (double)N);
+    if (S1) S1[i] = from_i128(s1 + N * h0);
+    if (S2) S2[i] = from_i128(s2 + 2 * h0 * s1 + N * h0 * h0);
+    if (H0) H0[i] = c.H0;
+  }
   return OKZ_OK;
 }
 

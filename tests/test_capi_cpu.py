@@ -111,3 +111,9 @@ def test_band_rows_checked_before_touching_cuda(okz, fuse, band):
         okz.okz_create_ex(prm)
     assert e.value.status == okz.OKZ_EINVAL
     assert "band_rows" in okz.okz_last_error()
+
+
+def test_growth_series_rejects_a_null_simulation(okz):
+    with pytest.raises(okz.OkzError) as e:
+        okz.okz_growth_series(None, [0, 1])
+    assert e.value.status == okz.OKZ_EINVAL

@@ -322,6 +322,28 @@ def test_one_cta_kernel_size_rule(okz):
         assert e.value.status == okz.OKZ_EUNSUPPORTED
 
 
+@pytest.mark.parametrize("L,kernel,p,q", [(4096, 4, 1.0, 0.0), (4096, 4, 0.75, 0.25),
+                                          (480, 3, 0.95, 0.05), (256, 5, 1.0, 1.0)])
+def test_growth_series_call_matches_per_sample_reads(okz, orc, L, kernel, p, q):
+    """okz_growth_series (sweeps and sums queued, one synchronisation)
+    gives, at every sample time, the sums okz_width2 reads one by one, and
+    the oracle's."""
+    times = [0, 1, 3, 4, 9, 16, 17, 30]
+    with okz.Simulation(L, p, q, seed=91, kernel=kernel) as a, \
+            okz.Simulation(L, p, q, seed=91, kernel=kernel) as b:
+        rec = a.growth_series(times)
+        ref = orc.Sim(L, p, q, 91)
+        for (t, H0, S1, S2, W2) in rec:
+            b.sweep(t - b.info().t)
+            ref.sweep(t - ref.t)
+            assert (S1, S2, W2) == b.width2() and H0 == b.info().H0, t
+            assert (S1, S2) == ref.sums() and W2 == ref.width2() and H0 == ref.H0, t
+        assert a.info().t == 30
+        with pytest.raises(okz.OkzError) as e:
+            a.growth_series([29])  # before the current sweep count
+        assert e.value.status == okz.OKZ_EINVAL
+
+
 def test_growth_series_helper_matches_oracle(okz, orc):
     """analysis.growth_series (the product's sampling loop) at L = 256,
     1000 sweeps, 20 samples: every record equals the oracle's."""
