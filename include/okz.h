@@ -279,6 +279,23 @@ okz_status okz_state(okz_sim *sim, uint32_t *planes_out, int out_is_device,
 okz_status okz_restore(okz_sim *sim, const uint32_t *planes, int in_is_device,
                        int64_t H0, uint64_t t);
 
+/* okz_restore from host memory in two halves, so that the host-to-device
+ * copy of the next state can run while the simulation sweeps.
+ * okz_stage_host starts copying planes (layout above, 2*L*L/8 bytes) into a
+ * staging buffer of that size that the simulation owns (made on first use,
+ * counted in okz_info's device_bytes, freed by okz_destroy) on a copy stream
+ * of its own, after the previous staged planes have been converted, and
+ * returns at once.
+ * okz_restore_staged makes the simulation's stream wait for that copy, then
+ * replaces the state with the staged planes, H0 and t (as okz_restore) on
+ * that stream, and returns at once. The host planes must stay unchanged until
+ * the copy has run: any later synchronizing call on the simulation
+ * (okz_synchronize, okz_width2, ...) guarantees it. Pinned host memory makes
+ * the copy asynchronous. Errors: EINVAL (null arguments, odd H0, t past
+ * 2^32 - 1, nothing staged), ENOMEM, ECUDA. */
+okz_status okz_stage_host(okz_sim *sim, const uint32_t *planes);
+okz_status okz_restore_staged(okz_sim *sim, int64_t H0, uint64_t t);
+
 /* okz_tune_stream -- the paper has no counterpart to this entry point (the
  * tiling of the update is this build's). Autotuner of the stream kernels'
  * launch shape for one workload: for every valid words_per_thread (4, 8, 16),

@@ -67,6 +67,8 @@ _SIGS = {
     "okz_sweep": (_c.c_int, [_vp, _c.c_int64]),
     "okz_sweep_rs": (_c.c_int, [_vp, _c.c_int64]),
     "okz_growth_series": (_c.c_int, [_vp, _c.c_int32, _vp, _vp, _vp, _vp, _vp]),
+    "okz_stage_host": (_c.c_int, [_vp, _vp]),
+    "okz_restore_staged": (_c.c_int, [_vp, _c.c_int64, _c.c_uint64]),
     "okz_width2": (_c.c_int, [_vp, _c.POINTER(okz_i128), _c.POINTER(okz_i128),
                               _c.POINTER(_c.c_double)]),
     "okz_moments": (_c.c_int, [_vp, _c.POINTER(okz_i128), _c.POINTER(_c.c_double),
@@ -425,6 +427,21 @@ class Simulation:
 
     def synchronize(self):
         okz_synchronize(self.h)
+
+    def stage_host(self, planes):
+        """Starts the host-to-device copy of `planes` (a CPU tensor or array,
+        slope-plane layout; kept alive here until the next stage_host)."""
+        if isinstance(planes, np.ndarray):
+            planes = np.ascontiguousarray(planes, dtype=np.uint32)
+            ptr = planes.ctypes.data
+        else:
+            assert planes.is_contiguous() and not planes.is_cuda, "host planes expected"
+            ptr = planes.data_ptr()
+        self._staged_host = planes
+        _check(lib().okz_stage_host(self.h, ptr), "okz_stage_host")
+
+    def restore_staged(self, H0, t):
+        _check(lib().okz_restore_staged(self.h, int(H0), int(t)), "okz_restore_staged")
 
     def growth_series(self, times):
         """[(t, H0, S1, S2, W2)] at every sample time, in one call."""

@@ -41,6 +41,13 @@ struct okz_sim {
   cudaGraphExec_t sweep_graph;
   int graph_state;
   uint64_t graph_replays;
+  // okz_stage_host / okz_restore_staged (made on first use): a device copy of
+  // caller planes taken on copy_stream; `staged` is recorded after the copy,
+  // `consumed` on the simulation's stream after the conversion has read it
+  uint32_t *stage_buf;
+  cudaStream_t copy_stream;
+  cudaEvent_t staged_ev, consumed_ev;
+  bool stage_pending;
 };
 
 namespace okz {
@@ -908,6 +915,70 @@ okz_status okz_restore(okz_sim *sim, const uint32_t *planes, int in_is_device, i
   return OKZ_OK;
 }
 
+okz_status okz_stage_host(okz_sim *sim, const uint32_t *planes) {
+  if (!sim || !planes) {
+    set_error("okz_stage_host: null simulation or planes");
+    return OKZ_EINVAL;
+  }
+  cudaError_t e = cudaSuccess;
+  if (!sim->stage_buf) {
+    e = cudaMalloc((void **)&sim->stage_buf, sim->lay.planes_bytes);
+    if (e != cudaSuccess) {
+      sim->stage_buf = nullptr;
+      cudaGetLastError();
+      set_error("okz_stage_host: cannot allocate the staging buffer");
+      return OKZ_ENOMEM;
+    }
+    e = cudaStreamCreateWithFlags(&sim->copy_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sim->staged_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sim->consumed_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(sim->consumed_ev, sim->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "okz_stage_host set-up");
+  }
+  // the previous staged planes must have been converted before they are overwritten
+  e = cudaStreamWaitEvent(sim->copy_stream, sim->consumed_ev, 0);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(sim->stage_buf, planes, sim->lay.planes_bytes, cudaMemcpyHostToDevice,
+                        sim->copy_stream);
+  if (e == cudaSuccess) e = cudaEventRecord(sim->staged_ev, sim->copy_stream);
+  if (e != cudaSuccess) return cuda_fail(e, "okz_stage_host copy");
+  sim->stage_pending = true;
+  return OKZ_OK;
+}
+
+okz_status okz_restore_staged(okz_sim *sim, int64_t H0, uint64_t t) {
+  if (!sim || t > 0xFFFFFFFFull) {
+    set_error("bad restore request");
+    return OKZ_EINVAL;
+  }
+  if (!sim->stage_pending) {
+    set_error("okz_restore_staged: nothing staged (okz_stage_host first)");
+    return OKZ_EINVAL;
+  }
+  if (H0 & 1) {
+    set_error("H0 = h(0,0) must be even (h(x,y) == x + y mod 2)");
+    return OKZ_EINVAL;
+  }
+  long long h0 = H0;
+  cudaError_t e = cudaStreamWaitEvent(sim->stream, sim->staged_ev, 0);
+  if (e == cudaSuccess) {
+    if (sim->parity)
+      e = launch_from_slopes(sim->stage_buf, sim->prm.L, h0, sim->hcol, sim->planes[sim->cur],
+                             sim->stream);
+    else
+      e = cudaMemcpyAsync(sim->planes[sim->cur], sim->stage_buf, sim->lay.planes_bytes,
+                          cudaMemcpyDeviceToDevice, sim->stream);
+  }
+  // a pageable source: the value is taken before the call returns
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&sim->ctrl->H0, &h0, sizeof(h0), cudaMemcpyHostToDevice, sim->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(sim->consumed_ev, sim->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "okz_restore_staged");
+  sim->stage_pending = false;
+  sim->t = t;
+  return OKZ_OK;
+}
+
 okz_status okz_get_info(okz_sim *sim, okz_info *info) {
   if (!sim || !info) {
     set_error("null argument");
@@ -925,7 +996,7 @@ okz_status okz_get_info(okz_sim *sim, okz_info *info) {
   info->kernel = sim->kernel;
   info->P = sim->acc.P;
   info->Q = sim->acc.Q;
-  info->device_bytes = sim->lay.total;
+  info->device_bytes = sim->lay.total + (sim->stage_buf ? sim->lay.planes_bytes : 0);
   info->words_per_thread = sim->wpt;
   info->sweeps_per_pass = sim->fuse;
   info->band_rows = sim->band_rows;
@@ -1015,6 +1086,14 @@ okz_status okz_tune_stream(const okz_params *prm, int32_t probe_sweeps, int32_t 
 okz_status okz_destroy(okz_sim *sim) {
   if (!sim) return OKZ_OK;
   cudaError_t e = cudaStreamSynchronize(sim->stream);
+  if (sim->copy_stream) {
+    cudaError_t e2 = cudaStreamSynchronize(sim->copy_stream);
+    if (e == cudaSuccess) e = e2;
+    cudaStreamDestroy(sim->copy_stream);
+  }
+  if (sim->staged_ev) cudaEventDestroy(sim->staged_ev);
+  if (sim->consumed_ev) cudaEventDestroy(sim->consumed_ev);
+  if (sim->stage_buf) cudaFree(sim->stage_buf);
   if (sim->sweep_graph) cudaGraphExecDestroy(sim->sweep_graph);
   if (sim->own_mem) cudaFree(sim->base);
   if (sim->own_stream) cudaStreamDestroy(sim->stream);

@@ -676,3 +676,30 @@ def test_moments_enqueue_then_fetch(okz, orc):
         assert sim.moments_fetch() == direct
         assert direct[0] == ref.power_sums()
         assert sim.moments() != direct  # the later sweeps are there
+
+
+@pytest.mark.parametrize("L,kernel", [(4096, 4), (4096, 2), (256, 5), (480, 3)])
+def test_staged_restore_equals_restore(okz, orc, L, kernel):
+    """okz_stage_host + okz_restore_staged give the state okz_restore gives,
+    also when the next copy is staged while the simulation sweeps."""
+    ref = orc.Sim(L, 0.75, 0.25, 5)
+    ref.sweep(6)
+    Xw, Yw = ref.packed()
+    planes = np.stack([Xw, Yw]).astype(np.uint32)
+    with okz.Simulation(L, 0.75, 0.25, seed=5, kernel=kernel) as a, \
+            okz.Simulation(L, 0.75, 0.25, seed=5, kernel=kernel) as b:
+        a.stage_host(planes)
+        a.restore_staged(ref.H0, ref.t)
+        a.stage_host(planes)        # staged while the sweeps below run
+        a.sweep(5)
+        b.restore(planes, ref.H0, ref.t)
+        b.sweep(5)
+        assert a.width2() == b.width2()
+        pa, ha, ta = a.state()
+        pb, hb, tb = b.state()
+        assert np.array_equal(pa, pb) and (ha, ta) == (hb, tb)
+        a.restore_staged(ref.H0, ref.t)  # the second copy: the same input again
+        _compare(a, ref)
+        with pytest.raises(okz.OkzError) as e:
+            a.restore_staged(ref.H0, ref.t)  # nothing staged
+        assert e.value.status == okz.OKZ_EINVAL
