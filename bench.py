@@ -66,8 +66,8 @@ N_SMS = 152
 #   ddrs_kernel           L = 32768, one launch = 1 sweep
 #   profile_count_tma_kernel  L = 65536, one profile pass
 TRAFFIC = {
-    "parity": ((556844800 + 485688064) / 65536 ** 2, "parity.cu",
-               "7cb3b808cb3c3d5fabbbec85770cac2fb0b6ed80ff42eb0e57d46b543f88c4da"),
+    "parity": ((556843776 + 485715712) / 65536 ** 2, "parity.cu",
+               "e29e46a778ebb22ec2a03d0910a177888edf726235022931eac4cb378c57854b"),
     "ddrs": ((134544640 + 73219072) / 32768 ** 2, "ddrs.cu",
              "c2f242e7e5e1b6fc82f8f918aac71218c2f2182050306070f95ae2ed2e30a831"),
     "profile": ((546672384 + 8760064) / 65536 ** 2, "psd.cu",
@@ -412,6 +412,17 @@ def run_gpu(args, world, rank, local):
 
     e2e_run(1)
     torch.cuda.synchronize(dev)
+    # context, not part of the number: this box's rate for a plain copy of
+    # the same pinned buffer to the device (the copy the pipeline hides
+    # behind each step's sweeps)
+    probe = torch.empty_like(host_planes, device=dev)
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    c0.record()
+    probe.copy_(host_planes, non_blocking=True)
+    c1.record()
+    c1.synchronize()
+    h2d_probe_gbs = host_planes.numel() * 4 / (c0.elapsed_time(c1) / 1e3) / 1e9
+    del probe
     _barrier(world)
     e2e_clocks = ClockSampler(local)
     e2e_clocks.start()
@@ -495,6 +506,7 @@ def run_gpu(args, world, rank, local):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": e2e_steps, "clocks": e2e_clk,
                 "ms_per_step": e2e_s / e2e_steps * 1e3,
+                "h2d_probe_gbs": h2d_probe_gbs,
 
                 "path": "okz_stage_host(pinned host planes; the next step's copy overlaps "
                         "this step's sweeps) + okz_restore_staged + okz_sweep + okz_width2 "
