@@ -66,8 +66,8 @@ N_SMS = 152
 #   ddrs_kernel           L = 32768, one launch = 1 sweep
 #   profile_count_tma_kernel  L = 65536, one profile pass
 TRAFFIC = {
-    "parity": ((556843776 + 485715712) / 65536 ** 2, "parity.cu",
-               "e29e46a778ebb22ec2a03d0910a177888edf726235022931eac4cb378c57854b"),
+    "parity": ((556842752 + 485629440) / 65536 ** 2, "parity.cu",
+               "8bfee5abbe3e121769d161b3fa46dd2a2ca84937c0335548879cf05254a9b8c3"),
     "ddrs": ((134544640 + 73219072) / 32768 ** 2, "ddrs.cu",
              "c2f242e7e5e1b6fc82f8f918aac71218c2f2182050306070f95ae2ed2e30a831"),
     "profile": ((546672384 + 8760064) / 65536 ** 2, "psd.cu",
@@ -716,6 +716,7 @@ def run_rs(args, world, rank, local):
     with torch.cuda.stream(stream):
         sim = okz.Simulation(L, 1.0, 0.0, seed=SEED + rank, torch_buffer=True,
                              kernel=okz.OKZ_KERNEL_PARITY_PLAIN)
+    peak_meas = measure_alu_peak(okz, local, stream.cuda_stream)
     for _ in range(args.warmup):
         sim.sweep_rs(per_step)
         sim.width2()
@@ -740,7 +741,7 @@ def run_rs(args, world, rank, local):
     launch_s = sum(a.elapsed_time(b) for a, b in evs) / 1e3 / (steps * per_step)
     value = world * N * per_step * steps / (ms / 1e3) / 1e9
     sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
-    alu_peak = N_SMS * ALU_LANES_PER_SM * sm_mhz * 1e6 / 1e12
+    alu_peak = _alu_peak_at(peak_meas, sm_mhz)
     alu_ops = RS_ALU_OPS_PER_ATTEMPT * N
     sim.close()
     if rank != 0:
@@ -758,7 +759,10 @@ def run_rs(args, world, rank, local):
         "roofline": {"bound": "alu", "achieved": alu_ops / launch_s / 1e12, "peak": alu_peak,
                      "unit": "Tops/s", "frac": alu_ops / launch_s / 1e12 / alu_peak,
                      "traffic": _traffic("ddrs", N), "kernel": "ddrs_kernel",
-                     "peak_kind": "derived: 152 SMs x 64 INT32 lanes x sampled SM clock",
+                     "peak_kind": "measured: okz_alu_peak on this GPU, scaled to the timed "
+                                  "region's SM clock",
+                     "peak_measured": peak_meas,
+                     "peak_derived": N_SMS * ALU_LANES_PER_SM * sm_mhz * 1e6 / 1e12,
                      "ops_per_launch": alu_ops, "launch_ms": launch_s * 1e3},
         "gpu_launches": steps * (per_step + 3),
         "clocks": clk,

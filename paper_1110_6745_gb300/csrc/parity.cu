@@ -294,22 +294,36 @@ __device__ __forceinline__ void pstage_gen(const uint32_t c[WPT], uint32_t lbit,
   }
   *mn0 = mn[0];
   if (SP == 0) m = 0;
+  // the first half draws two levels per test at 4 words per thread: two
+  // independent Philox chains in flight (a level drawn beyond the last
+  // undecided candidate changes nothing decided)
+  constexpr int LV = (SP == 0 && WPT == 4) ? 2 : 1;
   while (m < acc.k) {
     uint32_t open = 0;
 #pragma unroll
     for (int j = 0; j < WPT; ++j) open |= (ep[j] & mn[j]) | (eq[j] & mx[j]);
     if (SP == 0 ? !__any_sync(0xFFFFFFFFu, open != 0u) : open == 0u) break;
-    const uint32_t pb = (gb.pw >> (31 - m)) & 1u, qb = (gb.qw >> (31 - m)) & 1u;
+    const int nl = (LV == 2 && m + 1 < acc.k) ? 2 : 1;
+    u32x4 bl[LV][NG];
 #pragma unroll
-    for (int gq = 0; gq < NG; ++gq) {
-      const u32x4 b = philox10_rk(g0 + gq, 0u, t, (uint32_t)m, rk);
+    for (int v = 0; v < LV; ++v)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        lt_step(b.v[j], pb, lp[4 * gq + j], ep[4 * gq + j]);
-        lt_step(b.v[j], qb, lq[4 * gq + j], eq[4 * gq + j]);
-      }
+      for (int gq = 0; gq < NG; ++gq)
+        if (v < nl) bl[v][gq] = philox10_rk(g0 + gq, 0u, t, (uint32_t)(m + v), rk);
+#pragma unroll
+    for (int v = 0; v < LV; ++v) {
+      if (v >= nl) break;
+      const int mv = m + v;
+      const uint32_t pb = (gb.pw >> (31 - mv)) & 1u, qb = (gb.qw >> (31 - mv)) & 1u;
+#pragma unroll
+      for (int gq = 0; gq < NG; ++gq)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          lt_step(bl[v][gq].v[j], pb, lp[4 * gq + j], ep[4 * gq + j]);
+          lt_step(bl[v][gq].v[j], qb, lq[4 * gq + j], eq[4 * gq + j]);
+        }
     }
-    ++m;
+    m += nl;
   }
 #pragma unroll
   for (int j = 0; j < WPT; ++j) o[j] = c[j] ^ ((lp[j] & mn[j]) | (lq[j] & mx[j]));
