@@ -870,7 +870,8 @@ def run_steady(args, world, rank, local):
         tx = L ** 1.61
         burn, every = int(burn_tx * tx), int(every_tx * tx)
         t1 = time.perf_counter()
-        w = steady_state_w2(L, R, burn, nsamp, every, seed0=100000 + 1000 * L + 10 ** 6 * rank)
+        w = steady_state_w2(L, R, burn, nsamp, every, seed0=100000 + 1000 * L + 10 ** 6 * rank,
+                            tune=True)
         secs[L] = time.perf_counter() - t1
         k = w2_cumulants(w)
         samples[L], ratios[L] = w, k[1] / k[0] ** 2

@@ -51,12 +51,15 @@ def psi(samples, bins=50):
     return 0.5 * (edges[1:] + edges[:-1]), dens
 
 
-def steady_state_w2(L, replicas, burnin, nsamples, every, p=1.0, q=0.0, seed0=0):
+def steady_state_w2(L, replicas, burnin, nsamples, every, p=1.0, q=0.0, seed0=0, tune=False):
     """W^2 samples (replicas x nsamples) of `replicas` independent lattices of
     size L (seeds seed0 + r), each run `burnin` sweeps from the striped start
-    and then sampled every `every` sweeps."""
+    and then sampled every `every` sweeps. With `tune` the batch's launch shape
+    is autotuned first (results do not depend on it)."""
     with okz.Batch([L] * replicas, [p] * replicas, [q] * replicas,
                    [seed0 + r for r in range(replicas)]) as b:
+        if tune:
+            b.autotune(probe_sweeps=2)
         _advance(b, replicas, burnin)
         out = np.empty((replicas, nsamples))
         for k in range(nsamples):
