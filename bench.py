@@ -66,8 +66,8 @@ N_SMS = 152
 #   ddrs_kernel           L = 32768, one launch = 1 sweep
 #   profile_count_tma_kernel  L = 65536, one profile pass
 TRAFFIC = {
-    "parity": ((556842752 + 485629440) / 65536 ** 2, "parity.cu",
-               "8bfee5abbe3e121769d161b3fa46dd2a2ca84937c0335548879cf05254a9b8c3"),
+    "parity": ((556842496 + 485700608) / 65536 ** 2, "parity.cu",
+               "e885ebdca0a5071622570b2e9ae60d759de864158c4595e2eadbb60e3896aa8a"),
     "ddrs": ((134544640 + 73219072) / 32768 ** 2, "ddrs.cu",
              "c2f242e7e5e1b6fc82f8f918aac71218c2f2182050306070f95ae2ed2e30a831"),
     "profile": ((546672384 + 8760064) / 65536 ** 2, "psd.cu",

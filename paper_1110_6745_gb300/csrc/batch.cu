@@ -104,7 +104,8 @@ __device__ __forceinline__ void group_update(uint32_t *B, int L, int W, uint32_t
 
 // ---- band wavefront (lattices with L % 128 == 0) ----
 //
-// Every random level of R6 is keyed by (group, sweep, level), never by the
+// The random words of level m of 128-site group g in sweep t are Philox
+// (g, 0, t, m): every level is keyed by group, sweep and level, never by the
 // half-sweep, and a site is active in one half-sweep only: the levels a group
 // draws for its first-half candidates decide its second-half sites just as
 // well, as far as they go. So the first half-sweep of a group advances the

@@ -253,8 +253,9 @@ __device__ __forceinline__ uint32_t rotl1(uint32_t x) { return __funnelshift_l(x
 __device__ __forceinline__ uint32_t rotr1(uint32_t x) { return __funnelshift_r(x, x, 1); }
 
 // General k (random levels drawn lazily), one stage of half-sweep parity SP.
-// R6 keys a level by (group, sweep, level), never by the half-sweep, and a
-// site is active in one half-sweep only, so the levels the first half draws
+// The random words of level m of 128-site group g in sweep t are Philox
+// (g, 0, t, m): keyed by group, sweep and level, never by the half-sweep, and
+// a site is active in one half-sweep only, so the levels the first half draws
 // for its candidates decide the second half's sites as far as they go. SP = 0
 // starts every site of the words undecided and draws levels while any lane
 // of the warp has an undecided candidate (every lane runs every stage, and a
