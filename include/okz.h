@@ -280,7 +280,8 @@ okz_status okz_restore(okz_sim *sim, const uint32_t *planes, int in_is_device,
                        int64_t H0, uint64_t t);
 
 /* okz_restore from host memory in two halves, so that the host-to-device
- * copy of the next state can run while the simulation sweeps.
+ * copy of the next state can run while the simulation sweeps (the state is
+ * the slope planes of Sec. II; the paper has no counterpart to the split).
  * okz_stage_host starts copying planes (layout above, 2*L*L/8 bytes) into a
  * staging buffer of that size that the simulation owns (made on first use,
  * counted in okz_info's device_bytes, freed by okz_destroy) on a copy stream
